@@ -1,0 +1,155 @@
+/*
+ * lbnlm.h -- C ABI of the GB300 lattice-Boltzmann library for the tensorial nonlinear
+ * generalized Maxwell (nlM) fluid of Papenkort & Voigtmann, arXiv:1310.7450.
+ *
+ * One library call advances one or many independent 2-D channels with the paper's scheme:
+ * D2Q9 pull-streaming with half-way bounce-back walls (Sec. II B), the BGK collision with
+ * the non-Newtonian forcing term of Eq. (bodyforce), the flow-induced density of Eq. (rhoplus),
+ * three-point velocity gradients (Sec. II C) and the nlM stress of Eqs. (sigtsum, smalld,
+ * nlmaxwell).  All of a step runs in CUDA kernels of this library on the caller's stream.
+ *
+ * Conventions
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3.  D2Q9 numbering: 0:(0,0) 1:(1,0) 2:(0,1)
+ *     3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *   - Channel c has nx columns (x periodic) and ny[c] fluid rows; walls sit half-way below row
+ *     0 and above row ny[c]-1, so the width is 2H = ny[c].
+ *   - "Node order" of every field array: channel after channel, inside a channel row-major
+ *     (y outer, x inner): node = node_offset(c) + y*nx + x, node_offset(c) = nx * sum_{c'<c} ny[c'].
+ *   - "Plane order" of population arrays: channel after channel, inside a channel 9 planes
+ *     (direction i) of ny[c]*nx values in row-major order.
+ *   - Ownership: the handle owns all device state; every output buffer is the caller's
+ *     (host memory unless on_device != 0, then device memory of the handle's device); the
+ *     CUDA stream is borrowed and must outlive the handle.
+ *   - Errors: every call returns an lb_status; nothing throws across the ABI.  lb_last_error()
+ *     gives a human-readable detail of the most recent failure on the calling thread.
+ *   - Asynchrony: lb_step only enqueues work on the stream.  Calls that return host data
+ *     (lb_get_fields to host, lb_residual, lb_monitor, lb_channel_status, lb_get_*) synchronise
+ *     the stream first.
+ */
+#ifndef LBNLM_H
+#define LBNLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_handle lb_handle; /* opaque, library-owned */
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,     /* bad argument: null pointer, size, tau_lb <= 1/2, ny < 3, NaN, ... */
+    LB_ENOMEM = 2,     /* device or host allocation failed                                  */
+    LB_ECUDA = 3,      /* a CUDA call or kernel launch failed (detail in lb_last_error)       */
+    LB_EUNSTABLE = 4,  /* a channel produced NaN/Inf or |u| > 0.3; it is retired (not stepped) */
+    LB_ETIMEOUT = 5,   /* a bounded device-side wait gave up                                  */
+    LB_ESTATE = 6      /* the call needs state that does not exist yet (e.g. no residual)     */
+} lb_status;
+
+enum { LB_PREC_F64 = 0, LB_PREC_F32 = 1, LB_PREC_BF16 = 2 };
+enum { LB_STRESS_INLM = 0, LB_STRESS_TIMESTEPPED = 1 };
+enum { LB_GRID_STORE_SIGMA = 1 }; /* lb_grid.flags: write the 4-component stress every step */
+
+typedef struct {
+    int n_channels;   /* >= 1                                                              */
+    int nx;           /* periodic length shared by all channels, >= 1                      */
+    const int *ny;    /* [n_channels] fluid rows per channel, each >= 3 (copied)           */
+    int precision;    /* LB_PREC_F64: FP64 storage and arithmetic;
+                         LB_PREC_F32: populations stored as FP32 deviations n_i - w_i, FP32 math;
+                         LB_PREC_BF16: BF16 deviations, FP32 math                           */
+    int stress_mode;  /* LB_STRESS_INLM: instantaneous nlM stress, Eq. (sigtsum) (the paper's
+                         model, Sec. III A); LB_STRESS_TIMESTEPPED: one backward-Euler step of
+                         the upper-convected Maxwell equation Eq. (gkder) per LB step           */
+    int flags;        /* LB_GRID_STORE_SIGMA or 0                                          */
+} lb_grid;
+
+/* Per-channel physical parameters (lattice units).  The BGK collision carries the Newtonian
+ * viscosity eta^N = rho0 (tau_lb - 1/2)/3 (Eq. taulb); the forcing adds
+ * Sigma^nN = sigma + (G_inf tau0 - eta^N) D (Sec. IV; = sigma - G_inf tau D when eta^N is the
+ * low-shear viscosity G_inf (tau + tau0)). */
+typedef struct {
+    double tau_lb;       /* BGK relaxation time, > 1/2                                      */
+    double g_x;          /* body-force density along x (constant; Sec. III B)               */
+    double G_inf;        /* plateau modulus, >= 0                                           */
+    double tau0;         /* microscopic time; eta_inf = G_inf tau0 (Eq. Sigmamodel), >= 0    */
+    double theta;        /* tau / tau0 (structural relaxation time tau = theta tau0), >= 0   */
+    double gamma_c;      /* critical strain of Eq. (nlmaxwell), > 0; +inf = no thinning     */
+    double rho0;         /* reference density of eta^N and of the initial state, > 0        */
+    double rho_pert_amp; /* initial rho = rho0 (1 + amp U(-1,1)), U from SplitMix64         */
+    uint64_t seed;       /* SplitMix64 seed; counter = y*nx + x + 1 within the channel       */
+} lb_params;
+
+typedef struct {
+    int walls;      /* must be 1: half-way bounce-back at both channel walls (Sec. II B)    */
+    int periodic_x; /* must be 1: periodic along the channel                                */
+} lb_boundary;
+
+/* Create the channels on the current CUDA device, allocate their state and initialise it to
+ * rest equilibrium n_i = w_i rho(r) with delta rho = 0 and zero polymer stress.
+ * params: [n_channels].  cuda_stream: a cudaStream_t (0 = legacy default stream).
+ * On failure *out is NULL and nothing is leaked. */
+lb_status lb_create(const lb_grid *grid, const lb_params *params, const lb_boundary *boundary,
+                    void *cuda_stream, lb_handle **out);
+
+/* Advance every stable channel by n >= 0 steps (Eq. lbupdate: stream, then collide with
+ * Eq. bodyforce).  The last two steps also save the velocity so that the last step can
+ * evaluate the one-step residual (lb_residual).  Returns LB_EUNSTABLE once any channel has
+ * been found unstable (the other channels keep being stepped). */
+lb_status lb_step(lb_handle *h, long n);
+
+/* Macroscopic fields of the current state: the velocity u = j/rho [node][2], the polymer
+ * stress sigma [node][4] as (xx, yy, zz, xy) with zz = 0 in 2-D flow, and the hydrodynamic
+ * density rho = sum_i (n* + n)/2 - delta rho [node] (Eq. rhoj) that the next collision uses.
+ * Any of u, sigma, rho may be NULL.  out_dtype: 0 = double, 1 = float.  on_device: the
+ * pointers are device memory (no synchronisation) or host memory (synchronises).  The state
+ * is not changed. */
+lb_status lb_get_fields(lb_handle *h, void *u, void *sigma, void *rho, int out_dtype, int on_device);
+
+/* Per-channel one-step residual ||u(t) - u(t-1)||_2 / ||u(t)||_2 of the state before the last
+ * step of the most recent lb_step call (warp/block reductions fused into that step).
+ * r: host [n_channels].  LB_ESTATE if no residual has been evaluated yet. */
+lb_status lb_residual(lb_handle *h, double *r);
+
+/* Per-channel diagnostics of the same evaluation, host [n_channels][4]:
+ * (residual, flux = sum over nodes of u_x / nx, max |u|, step index of the evaluated state). */
+lb_status lb_monitor(lb_handle *h, double *out);
+
+/* Change the body force of one channel (channel = -1: all), e.g. 0 for cessation. */
+lb_status lb_set_body_force(lb_handle *h, int channel, double g_x);
+
+/* Warm start: set every node to the equilibrium of the given hydrodynamic density and velocity
+ * (host, node order: u [node][2], rho [node]), with the population current chosen so that
+ * j = rho u including the half force of Eq. (rhoj).  drho (host [node], may be NULL = 0) sets
+ * the stored flow-induced density change delta rho(t-1).  The carried stress (stress mode 1)
+ * is reset to zero. */
+lb_status lb_set_fields(lb_handle *h, const double *u, const double *rho, const double *drho);
+
+/* Full FP64 populations n*_i in plane order, delta rho [node], and the carried stress of
+ * stress mode 1 in plane order of 3 planes (xx, xy, yy) per channel (may be NULL otherwise).
+ * Values are converted to / from the storage precision (deviations n_i - w_i). */
+lb_status lb_set_populations(lb_handle *h, const double *n, const double *drho, const double *sig3);
+lb_status lb_get_populations(lb_handle *h, double *n, double *drho, double *sig3);
+
+/* Checkpoint: the raw device state (populations in storage precision, delta rho, carried
+ * stress, step counter) as an opaque byte image of lb_state_bytes() bytes.  Restoring it into a
+ * handle created with the same grid continues bit-for-bit. */
+size_t lb_state_bytes(const lb_handle *h);
+lb_status lb_get_state(lb_handle *h, void *buf, size_t bytes);
+lb_status lb_set_state(lb_handle *h, const void *buf, size_t bytes);
+
+/* Per-channel status words (host [n_channels]): 0 = stable, 1 = unstable (retired). */
+lb_status lb_channel_status(lb_handle *h, int *status);
+
+long lb_step_count(const lb_handle *h);     /* steps taken since creation (or restored)      */
+size_t lb_num_nodes(const lb_handle *h);     /* total fluid nodes over all channels           */
+void lb_destroy(lb_handle *h);               /* synchronises the stream, frees everything     */
+const char *lb_strerror(lb_status s);
+const char *lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBNLM_H */

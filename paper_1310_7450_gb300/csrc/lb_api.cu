@@ -1,0 +1,813 @@
+// lb_api.cu -- the C ABI declared in include/lbnlm.h: handle management, state layout, launch
+// sequencing of the fused step, field output, residual reduction, checkpointing.
+//
+// Device layout of a handle (all channels in one allocation per field):
+//   every channel c owns planes of P[c] elements (P[c] >= nx*ny[c], padded to 64 elements);
+//   base[c] = sum_{c'<c} P[c'] is the channel's plane offset, so a field with k planes keeps
+//   plane j of channel c at  k*base[c] + j*P[c].  Populations: 9 planes (ping-pong A/B);
+//   delta rho: 1 plane; carried stress (mode 1): 3 planes; stress output: 4 planes; saved
+//   velocity: 2 planes.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lb_step_tile.cuh"
+#include "lbnlm.h"
+
+namespace lbk {
+extern template cudaError_t launch_step_tile<double, double, 0>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<double, double, 1>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<float, float, 0>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<float, float, 1>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<__nv_bfloat16, float, 0>(const StepArgs<__nv_bfloat16, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<__nv_bfloat16, float, 1>(const StepArgs<__nv_bfloat16, float>&, int, size_t, cudaStream_t);
+}  // namespace lbk
+
+using namespace lbk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+lb_status fail(lb_status s, const char* fmt, const char* detail = nullptr) {
+    std::snprintf(g_err, sizeof g_err, fmt, detail ? detail : "");
+    return s;
+}
+lb_status cuda_fail(cudaError_t e, const char* where) {
+    std::snprintf(g_err, sizeof g_err, "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;
+}
+#define LB_CK(call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);      \
+    } while (0)
+
+constexpr int kThreads = 256;        // threads per CTA of the tile kernel
+constexpr double kGuard = 0.3;       // |u| above which a channel is declared unstable
+
+// SplitMix64 (Steele, Lea & Flood 2014; 64-bit finaliser as published by Vigna): output number
+// `counter` (>= 1) of the stream seeded with `seed`.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+    uint64_t z = seed + counter * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct InitChan {
+    long long base, P;
+    int ny, pad_;
+    double rho0, amp;
+    uint64_t seed;
+};
+
+// Rest equilibrium n_i = w_i rho(r), rho = rho0 (1 + amp U(-1,1)); delta rho = 0.
+template <typename T, typename C>
+__global__ void k_init(T* pop, C* drho, C* sig3, const InitChan* ch, int nx, int smode) {
+    const InitChan c = ch[blockIdx.y];
+    const long long n = (long long)nx * c.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double rho = c.rho0;
+        if (c.amp != 0.0) {
+            const uint64_t z = splitmix64(c.seed, (uint64_t)k + 1ull);
+            const double U = __dadd_rn(__dmul_rn((double)(z >> 11), 0x1p-52), -1.0);
+            rho = __dmul_rn(c.rho0, __dadd_rn(1.0, __dmul_rn(c.amp, U)));
+        }
+        const double dev = rho - 1.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Store<T>::st(pop + 9 * c.base + i * c.P + k, (C)(wgt<double>(i) * dev));
+        drho[c.base + k] = C(0);
+        if (smode == 1)
+            for (int j = 0; j < 3; ++j) sig3[3 * c.base + j * c.P + k] = C(0);
+    }
+}
+
+// Populations <-> full FP64 values in plane order (host staging is compact per channel).
+template <typename T, typename C>
+__global__ void k_pop_from_f64(T* pop, const double* src, const long long* base, const long long* P,
+                               const long long* node_off, const int* ny, int nx) {
+    const int c = blockIdx.y;
+    const long long n = (long long)nx * ny[c];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            Store<T>::st(pop + 9 * base[c] + i * P[c] + k, (C)(src[9 * node_off[c] + i * n + k] - wgt<double>(i)));
+}
+template <typename T, typename C>
+__global__ void k_pop_to_f64(const T* pop, double* dst, const long long* base, const long long* P,
+                             const long long* node_off, const int* ny, int nx) {
+    const int c = blockIdx.y;
+    const long long n = (long long)nx * ny[c];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            dst[9 * node_off[c] + i * n + k] = (double)Store<T>::ld(pop + 9 * base[c] + i * P[c] + k) + wgt<double>(i);
+}
+// k planes of a compact per-channel FP64 field <-> the padded C planes.
+template <typename C>
+__global__ void k_planes_from_f64(C* dst, const double* src, int kp, const long long* base, const long long* P,
+                                  const long long* node_off, const int* ny, int nx) {
+    const int c = blockIdx.y;
+    const long long n = (long long)nx * ny[c];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        for (int j = 0; j < kp; ++j) dst[kp * base[c] + j * P[c] + k] = (C)src[kp * node_off[c] + j * n + k];
+}
+template <typename C>
+__global__ void k_planes_to_f64(const C* src, double* dst, int kp, const long long* base, const long long* P,
+                                const long long* node_off, const int* ny, int nx) {
+    const int c = blockIdx.y;
+    const long long n = (long long)nx * ny[c];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        for (int j = 0; j < kp; ++j) dst[kp * node_off[c] + j * n + k] = (double)src[kp * base[c] + j * P[c] + k];
+}
+
+// Warm start: equilibrium of (rho, u - f/(2 rho)) so that j = sum c n + f/2 = rho u (Eq. rhoj).
+template <typename T, typename C>
+__global__ void k_set_fields(T* pop, C* drho, C* sig3, const double* u, const double* rho, const double* dr,
+                             const long long* base, const long long* P, const long long* node_off, const int* ny,
+                             const double* gx, int nx, int smode) {
+    const int c = blockIdx.y;
+    const long long n = (long long)nx * ny[c];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const long long node = node_off[c] + k;
+        const double r = rho[node];
+        const double ux = u[2 * node] - 0.5 * gx[c] / r, uy = u[2 * node + 1];
+        const double usq = ux * ux + uy * uy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double cu = cx(i) * ux + cy(i) * uy;
+            const double w = wgt<double>(i);
+            const double dev = w * ((r - 1.0) + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+            Store<T>::st(pop + 9 * base[c] + i * P[c] + k, (C)dev);
+        }
+        drho[base[c] + k] = dr ? (C)dr[node] : C(0);
+        if (smode == 1)
+            for (int j = 0; j < 3; ++j) sig3[3 * base[c] + j * P[c] + k] = C(0);
+    }
+}
+
+template <typename C>
+__global__ void k_set_gx(ChanParams<C>* chan, int n_ch, int ch, double gx) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_ch && (ch < 0 || c == ch)) chan[c].gx = (C)gx;
+}
+
+// Per-channel reduction of the step's block partials, in a fixed order (deterministic).
+__global__ void k_reduce_residual(const double* partials, const int* item_begin, const int* status, double* mon,
+                                  int nx, long long state_index) {
+    const int c = blockIdx.x;
+    const int b = item_begin[c], e = item_begin[c + 1];
+    __shared__ double red[kThreads][4];
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+        s0 += partials[4 * k];
+        s1 += partials[4 * k + 1];
+        s2 += partials[4 * k + 2];
+        s3 = fmax(s3, partials[4 * k + 3]);
+    }
+    red[threadIdx.x][0] = s0; red[threadIdx.x][1] = s1; red[threadIdx.x][2] = s2; red[threadIdx.x][3] = s3;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            red[threadIdx.x][0] += red[threadIdx.x + h][0];
+            red[threadIdx.x][1] += red[threadIdx.x + h][1];
+            red[threadIdx.x][2] += red[threadIdx.x + h][2];
+            red[threadIdx.x][3] = fmax(red[threadIdx.x][3], red[threadIdx.x + h][3]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const bool ok = status[c] == 0;
+        mon[4 * c + 0] = ok ? (red[0][1] > 0 ? sqrt(red[0][0] / red[0][1]) : 0.0) : NAN;
+        mon[4 * c + 1] = ok ? red[0][2] / nx : NAN;
+        mon[4 * c + 2] = ok ? red[0][3] : NAN;
+        mon[4 * c + 3] = (double)state_index;
+    }
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A* src, B* dst, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        dst[k] = (B)src[k];
+}
+
+int grid_for(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+}  // namespace
+
+struct lb_handle {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int n_ch = 0, nx = 0, prec = 0, smode = 0, flags = 0;
+    std::vector<int> ny;
+    std::vector<long long> P, base, node_off;
+    long long planes = 0;  // sum of P
+    long long nodes = 0;
+    std::vector<lb_params> params;
+    size_t tsize = 0, csize = 0;  // storage / arithmetic element sizes
+    // device state
+    void *popA = nullptr, *popB = nullptr, *drho = nullptr, *sig3 = nullptr, *sig4 = nullptr, *uprev = nullptr;
+    void* chan = nullptr;
+    WorkItem* items_d = nullptr;
+    int* item_begin_d = nullptr;
+    double* partials = nullptr;
+    double* mon_d = nullptr;
+    int* status_d = nullptr;
+    long long *base_d = nullptr, *P_d = nullptr, *node_off_d = nullptr;
+    int* ny_d = nullptr;
+    double* gx_d = nullptr;
+    void* fields = nullptr;    // staging for lb_get_fields, 7 values per node in C type
+    void* fconv = nullptr;     // staging for converted fields, 7 values per node
+    void* hstage = nullptr;    // device staging for FP64 host transfers
+    size_t hstage_bytes = 0;
+    // launch plan
+    std::vector<WorkItem> items;
+    std::vector<int> item_begin;
+    size_t smem = 0;
+    // bookkeeping
+    long step = 0;
+    long uprev_state = -10;    // state index whose velocity u_prev holds
+    long mon_state = -1;       // state index of the last residual evaluation (-1: none)
+    int* status_h = nullptr;   // pinned
+    cudaEvent_t status_ev = nullptr;
+    bool status_pending = false;
+    bool any_unstable = false;
+};
+
+namespace {
+
+template <typename C>
+std::vector<ChanParams<C>> make_chan(const lb_handle* h) {
+    std::vector<ChanParams<C>> v(h->n_ch);
+    for (int c = 0; c < h->n_ch; ++c) {
+        const lb_params& p = h->params[c];
+        ChanParams<C> q{};
+        q.base = h->base[c];
+        q.P = h->P[c];
+        q.node_off = h->node_off[c];
+        q.ny = h->ny[c];
+        q.omega = (C)(1.0 / p.tau_lb);
+        q.k1 = (C)(-9.0 / (2.0 * p.tau_lb));
+        q.k2 = (C)(1.0 - 1.0 / (2.0 * p.tau_lb));
+        q.gx = (C)p.g_x;
+        q.G = (C)p.G_inf;
+        q.tau = (C)(p.theta * p.tau0);
+        q.inv_gc = std::isinf(p.gamma_c) ? C(0) : (C)(1.0 / p.gamma_c);
+        q.cD = (C)(p.G_inf * p.tau0 - p.rho0 * (p.tau_lb - 0.5) / 3.0);
+        v[c] = q;
+    }
+    return v;
+}
+
+// Tile plan: narrow channels (nx <= 64) use full-width tiles of at most kThreads/nx (>= 4) rows;
+// wide ones 32 x 8 tiles.  Row tiles are balanced: with ny >= 3 and a row target >= 4 every tile
+// gets between 2 and the target rows (one-sided differences at a wall need the two rows next to
+// it inside the tile or its halo), so a tile never holds more nodes than the CTA has threads.
+void plan_tiles(lb_handle* h) {
+    h->items.clear();
+    h->item_begin.assign(h->n_ch + 1, 0);
+    int maxEX = 0, maxEY = 0;
+    for (int c = 0; c < h->n_ch; ++c) {
+        h->item_begin[c] = (int)h->items.size();
+        const int ny = h->ny[c];
+        int nxt, nyt_target;
+        if (h->nx <= kThreads / 4) { nxt = h->nx; nyt_target = kThreads / h->nx; }
+        else { nxt = 32; nyt_target = kThreads / 32; }
+        const int ntx = (h->nx + nxt - 1) / nxt;
+        const int nty = (ny + nyt_target - 1) / nyt_target;
+        for (int ty = 0; ty < nty; ++ty) {
+            const int y0 = (int)((long long)ny * ty / nty), y1 = (int)((long long)ny * (ty + 1) / nty);
+            for (int tx = 0; tx < ntx; ++tx) {
+                WorkItem w{};
+                w.ch = c;
+                w.x0 = tx * nxt;
+                w.nxt = (tx == ntx - 1) ? h->nx - w.x0 : nxt;
+                if (ntx == 1) w.nxt = h->nx;
+                w.y0 = y0;
+                w.nyt = y1 - y0;
+                h->items.push_back(w);
+                const int EX = (w.nxt == h->nx) ? h->nx : w.nxt + 2;
+                if (EX > maxEX) maxEX = EX;
+                if (w.nyt + 2 > maxEY) maxEY = w.nyt + 2;
+            }
+        }
+    }
+    h->item_begin[h->n_ch] = (int)h->items.size();
+    h->smem = (size_t)maxEX * maxEY * 2 * h->csize;
+}
+
+lb_status validate(const lb_grid* g, const lb_params* p, const lb_boundary* b) {
+    if (!g || !p || !b) return fail(LB_EINVAL, "lb_create: null argument%s");
+    if (g->n_channels < 1 || g->nx < 1 || !g->ny) return fail(LB_EINVAL, "lb_create: need n_channels >= 1, nx >= 1, ny%s");
+    if (g->precision < 0 || g->precision > 2) return fail(LB_EINVAL, "lb_create: unknown precision%s");
+    if (g->stress_mode < 0 || g->stress_mode > 1) return fail(LB_EINVAL, "lb_create: unknown stress_mode%s");
+    if (b->walls != 1 || b->periodic_x != 1)
+        return fail(LB_EINVAL, "lb_create: only bounce-back walls with periodic x are supported%s");
+    for (int c = 0; c < g->n_channels; ++c) {
+        if (g->ny[c] < 3) return fail(LB_EINVAL, "lb_create: ny must be >= 3%s");
+        if ((long long)g->ny[c] * g->nx > (1ll << 40)) return fail(LB_EINVAL, "lb_create: channel too large%s");
+        const lb_params& q = p[c];
+        const double v[8] = {q.tau_lb, q.g_x, q.G_inf, q.tau0, q.theta, q.rho0, q.rho_pert_amp, 0.0};
+        for (double x : v)
+            if (std::isnan(x) || std::isinf(x)) return fail(LB_EINVAL, "lb_create: non-finite parameter%s");
+        if (!(q.tau_lb > 0.5)) return fail(LB_EINVAL, "lb_create: tau_lb must be > 1/2%s");
+        if (q.G_inf < 0 || q.tau0 < 0 || q.theta < 0) return fail(LB_EINVAL, "lb_create: G_inf, tau0, theta must be >= 0%s");
+        if (!(q.gamma_c > 0)) return fail(LB_EINVAL, "lb_create: gamma_c must be > 0 (inf allowed)%s");
+        if (!(q.rho0 > 0) || q.rho_pert_amp < 0 || q.rho_pert_amp >= 1)
+            return fail(LB_EINVAL, "lb_create: need rho0 > 0 and 0 <= rho_pert_amp < 1%s");
+    }
+    return LB_OK;
+}
+
+template <typename T>
+void free_dev(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void release(lb_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_dev(h->popA); free_dev(h->popB); free_dev(h->drho); free_dev(h->sig3); free_dev(h->sig4);
+    free_dev(h->uprev); free_dev(h->chan); free_dev(h->items_d); free_dev(h->item_begin_d);
+    free_dev(h->partials); free_dev(h->mon_d); free_dev(h->status_d); free_dev(h->base_d); free_dev(h->P_d);
+    free_dev(h->node_off_d); free_dev(h->ny_d); free_dev(h->gx_d); free_dev(h->fields); free_dev(h->fconv);
+    free_dev(h->hstage);
+    if (h->status_h) cudaFreeHost(h->status_h);
+    if (h->status_ev) cudaEventDestroy(h->status_ev);
+    delete h;
+}
+
+lb_status ensure_hstage(lb_handle* h, size_t bytes) {
+    if (h->hstage_bytes >= bytes) return LB_OK;
+    free_dev(h->hstage);
+    h->hstage_bytes = 0;
+    LB_CK(cudaMalloc(&h->hstage, bytes));
+    h->hstage_bytes = bytes;
+    return LB_OK;
+}
+
+template <typename T, typename C>
+StepArgs<T, C> base_args(lb_handle* h) {
+    StepArgs<T, C> a{};
+    a.pin = (const T*)h->popA;
+    a.pout = (T*)h->popB;
+    a.drho = (C*)h->drho;
+    a.sig3 = (C*)h->sig3;
+    a.sig4 = (C*)h->sig4;
+    a.uprev = (C*)h->uprev;
+    a.partials = h->partials;
+    a.items = h->items_d;
+    a.chan = (const ChanParams<C>*)h->chan;
+    a.status = h->status_d;
+    a.nx = h->nx;
+    a.guard = (C)kGuard;
+    return a;
+}
+
+template <typename T, typename C>
+cudaError_t launch(lb_handle* h, const StepArgs<T, C>& a) {
+    const int n = (int)h->items.size();
+    if (h->smode == 0) return launch_step_tile<T, C, 0>(a, n, h->smem, h->stream);
+    return launch_step_tile<T, C, 1>(a, n, h->smem, h->stream);
+}
+
+template <typename T, typename C>
+lb_status run_steps(lb_handle* h, long n) {
+    for (long s = 1; s <= n; ++s) {
+        StepArgs<T, C> a = base_args<T, C>(h);
+        int f = 0;
+        if (h->flags & LB_GRID_STORE_SIGMA) f |= F_STORE_SIGMA;
+        const bool resid = (s == n) && (h->uprev_state == h->step - 1);
+        if (s >= n - 1) f |= F_SAVE_U;
+        if (resid) f |= F_RESID;
+        a.flags = f;
+        LB_CK((launch<T, C>(h, a)));
+        if (resid) {
+            k_reduce_residual<<<h->n_ch, kThreads, 0, h->stream>>>(h->partials, h->item_begin_d, h->status_d,
+                                                                    h->mon_d, h->nx, h->step);
+            LB_CK(cudaGetLastError());
+            h->mon_state = h->step;
+        }
+        if (f & F_SAVE_U) h->uprev_state = h->step;
+        std::swap(h->popA, h->popB);
+        ++h->step;
+    }
+    return LB_OK;
+}
+
+template <typename T, typename C>
+lb_status fields_pass(lb_handle* h, C* fu, C* fs, C* fr) {
+    StepArgs<T, C> a = base_args<T, C>(h);
+    a.flags = F_FIELDS;
+    a.fu = fu;
+    a.fsig = fs;
+    a.frho = fr;
+    LB_CK((launch<T, C>(h, a)));
+    return LB_OK;
+}
+
+lb_status poll_status(lb_handle* h, bool wait) {
+    if (h->status_pending) {
+        cudaError_t q = wait ? cudaEventSynchronize(h->status_ev) : cudaEventQuery(h->status_ev);
+        if (q == cudaSuccess) {
+            h->status_pending = false;
+            for (int c = 0; c < h->n_ch; ++c)
+                if (h->status_h[c]) h->any_unstable = true;
+        } else if (q != cudaErrorNotReady) {
+            return cuda_fail(q, "status event");
+        }
+    }
+    return LB_OK;
+}
+
+lb_status request_status(lb_handle* h) {
+    LB_CK(cudaMemcpyAsync(h->status_h, h->status_d, sizeof(int) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaEventRecord(h->status_ev, h->stream));
+    h->status_pending = true;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_last_error(void) { return g_err; }
+
+const char* lb_strerror(lb_status s) {
+    switch (s) {
+        case LB_OK: return "ok";
+        case LB_EINVAL: return "invalid argument";
+        case LB_ENOMEM: return "out of memory";
+        case LB_ECUDA: return "CUDA error";
+        case LB_EUNSTABLE: return "channel unstable";
+        case LB_ETIMEOUT: return "device wait timed out";
+        case LB_ESTATE: return "state not available";
+    }
+    return "unknown status";
+}
+
+lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_boundary* boundary, void* cuda_stream,
+                    lb_handle** out) {
+    if (!out) return fail(LB_EINVAL, "lb_create: out is null%s");
+    *out = nullptr;
+    lb_status st = validate(grid, params, boundary);
+    if (st != LB_OK) return st;
+    lb_handle* h = new (std::nothrow) lb_handle();
+    if (!h) return fail(LB_ENOMEM, "lb_create: host allocation%s");
+    auto bail = [&](lb_status s) { release(h); return s; };
+    cudaGetDevice(&h->dev);
+    h->stream = (cudaStream_t)cuda_stream;
+    h->n_ch = grid->n_channels;
+    h->nx = grid->nx;
+    h->prec = grid->precision;
+    h->smode = grid->stress_mode;
+    h->flags = grid->flags;
+    h->tsize = h->prec == LB_PREC_F64 ? 8 : (h->prec == LB_PREC_F32 ? 4 : 2);
+    h->csize = h->prec == LB_PREC_F64 ? 8 : 4;
+    h->ny.assign(grid->ny, grid->ny + h->n_ch);
+    h->params.assign(params, params + h->n_ch);
+    h->P.resize(h->n_ch); h->base.resize(h->n_ch); h->node_off.resize(h->n_ch);
+    long long acc = 0, nodes = 0;
+    for (int c = 0; c < h->n_ch; ++c) {
+        const long long n = (long long)h->nx * h->ny[c];
+        h->P[c] = (n + 63) / 64 * 64;
+        h->base[c] = acc;
+        h->node_off[c] = nodes;
+        acc += h->P[c];
+        nodes += n;
+    }
+    h->planes = acc;
+    h->nodes = nodes;
+    plan_tiles(h);
+
+    auto dmalloc = [&](void** p, size_t bytes) -> cudaError_t { return cudaMalloc(p, bytes < 16 ? 16 : bytes); };
+    cudaError_t e;
+#define LB_ALLOC(ptr, bytes)                                                   \
+    do {                                                                       \
+        e = dmalloc((void**)&(ptr), (bytes));                                  \
+        if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMalloc")); \
+    } while (0)
+    LB_ALLOC(h->popA, 9 * h->planes * h->tsize);
+    LB_ALLOC(h->popB, 9 * h->planes * h->tsize);
+    LB_ALLOC(h->drho, h->planes * h->csize);
+    if (h->smode == 1) LB_ALLOC(h->sig3, 3 * h->planes * h->csize);
+    if (h->flags & LB_GRID_STORE_SIGMA) LB_ALLOC(h->sig4, 4 * h->planes * h->csize);
+    LB_ALLOC(h->uprev, 2 * h->planes * h->csize);
+    LB_ALLOC(h->chan, h->n_ch * (h->csize == 8 ? sizeof(ChanParams<double>) : sizeof(ChanParams<float>)));
+    LB_ALLOC(h->items_d, h->items.size() * sizeof(WorkItem));
+    LB_ALLOC(h->item_begin_d, (h->n_ch + 1) * sizeof(int));
+    LB_ALLOC(h->partials, 4 * h->items.size() * sizeof(double));
+    LB_ALLOC(h->mon_d, 4 * h->n_ch * sizeof(double));
+    LB_ALLOC(h->status_d, h->n_ch * sizeof(int));
+    LB_ALLOC(h->base_d, h->n_ch * sizeof(long long));
+    LB_ALLOC(h->P_d, h->n_ch * sizeof(long long));
+    LB_ALLOC(h->node_off_d, h->n_ch * sizeof(long long));
+    LB_ALLOC(h->ny_d, h->n_ch * sizeof(int));
+    LB_ALLOC(h->gx_d, h->n_ch * sizeof(double));
+#undef LB_ALLOC
+    e = cudaMallocHost((void**)&h->status_h, h->n_ch * sizeof(int));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
+    e = cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaEventCreate"));
+
+    // tables (synchronous copies: creation is not on the hot path)
+    std::vector<double> gx(h->n_ch);
+    std::vector<InitChan> ic(h->n_ch);
+    for (int c = 0; c < h->n_ch; ++c) {
+        gx[c] = h->params[c].g_x;
+        ic[c] = InitChan{h->base[c], h->P[c], h->ny[c], 0, h->params[c].rho0, h->params[c].rho_pert_amp, h->params[c].seed};
+    }
+    InitChan* ic_d = nullptr;
+    e = cudaMalloc(&ic_d, sizeof(InitChan) * h->n_ch);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMalloc"));
+    bool ok = true;
+    ok &= cudaMemcpy(ic_d, ic.data(), sizeof(InitChan) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (h->csize == 8) {
+        auto v = make_chan<double>(h);
+        ok &= cudaMemcpy(h->chan, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    } else {
+        auto v = make_chan<float>(h);
+        ok &= cudaMemcpy(h->chan, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    ok &= cudaMemcpy(h->items_d, h->items.data(), sizeof(WorkItem) * h->items.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(h->item_begin_d, h->item_begin.data(), sizeof(int) * (h->n_ch + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(h->base_d, h->base.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(h->P_d, h->P.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(h->node_off_d, h->node_off.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(h->ny_d, h->ny.data(), sizeof(int) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(h->gx_d, gx.data(), sizeof(double) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemsetAsync(h->status_d, 0, sizeof(int) * h->n_ch, h->stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(h->uprev, 0, 2 * h->planes * h->csize, h->stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(h->popB, 0, 9 * h->planes * h->tsize, h->stream) == cudaSuccess;
+    if (h->sig4) ok &= cudaMemsetAsync(h->sig4, 0, 4 * h->planes * h->csize, h->stream) == cudaSuccess;
+    if (!ok) { cudaFree(ic_d); return bail(cuda_fail(cudaGetLastError(), "lb_create: table upload")); }
+    long long maxn = 0;
+    for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
+    dim3 g(grid_for(maxn), h->n_ch);
+    switch (h->prec) {
+        case LB_PREC_F64: k_init<double, double><<<g, 256, 0, h->stream>>>((double*)h->popA, (double*)h->drho, (double*)h->sig3, ic_d, h->nx, h->smode); break;
+        case LB_PREC_F32: k_init<float, float><<<g, 256, 0, h->stream>>>((float*)h->popA, (float*)h->drho, (float*)h->sig3, ic_d, h->nx, h->smode); break;
+        default: k_init<__nv_bfloat16, float><<<g, 256, 0, h->stream>>>((__nv_bfloat16*)h->popA, (float*)h->drho, (float*)h->sig3, ic_d, h->nx, h->smode); break;
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(ic_d);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: init kernel"));
+    *out = h;
+    return LB_OK;
+}
+
+void lb_destroy(lb_handle* h) { release(h); }
+
+long lb_step_count(const lb_handle* h) { return h ? h->step : -1; }
+size_t lb_num_nodes(const lb_handle* h) { return h ? (size_t)h->nodes : 0; }
+
+lb_status lb_step(lb_handle* h, long n) {
+    if (!h || n < 0) return fail(LB_EINVAL, "lb_step: bad handle or n%s");
+    lb_status st = poll_status(h, false);
+    if (st != LB_OK) return st;
+    if (n == 0) return h->any_unstable ? LB_EUNSTABLE : LB_OK;
+    switch (h->prec) {
+        case LB_PREC_F64: st = run_steps<double, double>(h, n); break;
+        case LB_PREC_F32: st = run_steps<float, float>(h, n); break;
+        default: st = run_steps<__nv_bfloat16, float>(h, n); break;
+    }
+    if (st != LB_OK) return st;
+    if (!h->status_pending) {
+        st = request_status(h);
+        if (st != LB_OK) return st;
+    }
+    return h->any_unstable ? LB_EUNSTABLE : LB_OK;
+}
+
+lb_status lb_get_fields(lb_handle* h, void* u, void* sigma, void* rho, int out_dtype, int on_device) {
+    if (!h || (out_dtype != 0 && out_dtype != 1)) return fail(LB_EINVAL, "lb_get_fields: bad handle or dtype%s");
+    if (!u && !sigma && !rho) return LB_OK;
+    const long long N = h->nodes;
+    if (!h->fields) LB_CK(cudaMalloc(&h->fields, 7 * N * h->csize));
+    char* base = (char*)h->fields;
+    void* fu = base;
+    void* fs = base + 2 * N * h->csize;
+    void* fr = base + 6 * N * h->csize;
+    lb_status st;
+    switch (h->prec) {
+        case LB_PREC_F64: st = fields_pass<double, double>(h, (double*)fu, (double*)fs, (double*)fr); break;
+        case LB_PREC_F32: st = fields_pass<float, float>(h, (float*)fu, (float*)fs, (float*)fr); break;
+        default: st = fields_pass<__nv_bfloat16, float>(h, (float*)fu, (float*)fs, (float*)fr); break;
+    }
+    if (st != LB_OK) return st;
+    const size_t osize = out_dtype == 0 ? 8 : 4;
+    const void* src = h->fields;
+    if (osize != h->csize) {
+        if (!h->fconv) LB_CK(cudaMalloc(&h->fconv, 7 * N * 8));
+        if (h->csize == 8) k_convert<double, float><<<grid_for(7 * N), 256, 0, h->stream>>>((const double*)h->fields, (float*)h->fconv, 7 * N);
+        else k_convert<float, double><<<grid_for(7 * N), 256, 0, h->stream>>>((const float*)h->fields, (double*)h->fconv, 7 * N);
+        LB_CK(cudaGetLastError());
+        src = h->fconv;
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const char* s = (const char*)src;
+    if (u) LB_CK(cudaMemcpyAsync(u, s, 2 * N * osize, kind, h->stream));
+    if (sigma) LB_CK(cudaMemcpyAsync(sigma, s + 2 * N * osize, 4 * N * osize, kind, h->stream));
+    if (rho) LB_CK(cudaMemcpyAsync(rho, s + 6 * N * osize, N * osize, kind, h->stream));
+    if (!on_device) LB_CK(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_monitor(lb_handle* h, double* out) {
+    if (!h || !out) return fail(LB_EINVAL, "lb_monitor: null argument%s");
+    if (h->mon_state < 0) return fail(LB_ESTATE, "lb_monitor: no residual evaluated yet (run lb_step with n >= 2)%s");
+    LB_CK(cudaMemcpyAsync(out, h->mon_d, 4 * h->n_ch * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_residual(lb_handle* h, double* r) {
+    if (!h || !r) return fail(LB_EINVAL, "lb_residual: null argument%s");
+    std::vector<double> m(4 * (size_t)h->n_ch);
+    lb_status st = lb_monitor(h, m.data());
+    if (st != LB_OK) return st;
+    for (int c = 0; c < h->n_ch; ++c) r[c] = m[4 * c];
+    return LB_OK;
+}
+
+lb_status lb_set_body_force(lb_handle* h, int channel, double g_x) {
+    if (!h || channel < -1 || channel >= h->n_ch || std::isnan(g_x) || std::isinf(g_x))
+        return fail(LB_EINVAL, "lb_set_body_force: bad argument%s");
+    for (int c = 0; c < h->n_ch; ++c)
+        if (channel < 0 || c == channel) h->params[c].g_x = g_x;
+    if (h->csize == 8) k_set_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->n_ch, channel, g_x);
+    else k_set_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->n_ch, channel, g_x);
+    LB_CK(cudaGetLastError());
+    std::vector<double> gx(h->n_ch);
+    for (int c = 0; c < h->n_ch; ++c) gx[c] = h->params[c].g_x;
+    LB_CK(cudaStreamSynchronize(h->stream));
+    LB_CK(cudaMemcpy(h->gx_d, gx.data(), sizeof(double) * h->n_ch, cudaMemcpyHostToDevice));
+    return LB_OK;
+}
+
+lb_status lb_set_fields(lb_handle* h, const double* u, const double* rho, const double* drho) {
+    if (!h || !u || !rho) return fail(LB_EINVAL, "lb_set_fields: null argument%s");
+    const long long N = h->nodes;
+    lb_status st = ensure_hstage(h, (size_t)N * 4 * sizeof(double));
+    if (st != LB_OK) return st;
+    double* su = (double*)h->hstage;
+    double* sr = su + 2 * N;
+    double* sd = su + 3 * N;
+    LB_CK(cudaMemcpyAsync(su, u, 2 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    LB_CK(cudaMemcpyAsync(sr, rho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (drho) LB_CK(cudaMemcpyAsync(sd, drho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    long long maxn = 0;
+    for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
+    dim3 g(grid_for(maxn), h->n_ch);
+    switch (h->prec) {
+        case LB_PREC_F64: k_set_fields<double, double><<<g, 256, 0, h->stream>>>((double*)h->popA, (double*)h->drho, (double*)h->sig3, su, sr, drho ? sd : nullptr, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode); break;
+        case LB_PREC_F32: k_set_fields<float, float><<<g, 256, 0, h->stream>>>((float*)h->popA, (float*)h->drho, (float*)h->sig3, su, sr, drho ? sd : nullptr, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode); break;
+        default: k_set_fields<__nv_bfloat16, float><<<g, 256, 0, h->stream>>>((__nv_bfloat16*)h->popA, (float*)h->drho, (float*)h->sig3, su, sr, drho ? sd : nullptr, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode); break;
+    }
+    LB_CK(cudaGetLastError());
+    LB_CK(cudaStreamSynchronize(h->stream));
+    h->uprev_state = -10;
+    return LB_OK;
+}
+
+lb_status lb_set_populations(lb_handle* h, const double* n, const double* drho, const double* sig3) {
+    if (!h || !n || !drho) return fail(LB_EINVAL, "lb_set_populations: null argument%s");
+    const long long N = h->nodes;
+    lb_status st = ensure_hstage(h, (size_t)N * 9 * sizeof(double));
+    if (st != LB_OK) return st;
+    long long maxn = 0;
+    for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
+    dim3 g(grid_for(maxn), h->n_ch);
+    double* s = (double*)h->hstage;
+    LB_CK(cudaMemcpyAsync(s, n, 9 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    switch (h->prec) {
+        case LB_PREC_F64: k_pop_from_f64<double, double><<<g, 256, 0, h->stream>>>((double*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
+        case LB_PREC_F32: k_pop_from_f64<float, float><<<g, 256, 0, h->stream>>>((float*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
+        default: k_pop_from_f64<__nv_bfloat16, float><<<g, 256, 0, h->stream>>>((__nv_bfloat16*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
+    }
+    LB_CK(cudaGetLastError());
+    LB_CK(cudaMemcpyAsync(s, drho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (h->csize == 8) k_planes_from_f64<double><<<g, 256, 0, h->stream>>>((double*)h->drho, s, 1, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+    else k_planes_from_f64<float><<<g, 256, 0, h->stream>>>((float*)h->drho, s, 1, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+    LB_CK(cudaGetLastError());
+    if (h->smode == 1) {
+        if (sig3) {
+            LB_CK(cudaStreamSynchronize(h->stream));
+            LB_CK(cudaMemcpyAsync(s, sig3, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            if (h->csize == 8) k_planes_from_f64<double><<<g, 256, 0, h->stream>>>((double*)h->sig3, s, 3, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+            else k_planes_from_f64<float><<<g, 256, 0, h->stream>>>((float*)h->sig3, s, 3, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+            LB_CK(cudaGetLastError());
+        } else {
+            LB_CK(cudaMemsetAsync(h->sig3, 0, 3 * h->planes * h->csize, h->stream));
+        }
+    }
+    LB_CK(cudaStreamSynchronize(h->stream));
+    h->uprev_state = -10;
+    return LB_OK;
+}
+
+lb_status lb_get_populations(lb_handle* h, double* n, double* drho, double* sig3) {
+    if (!h || !n || !drho) return fail(LB_EINVAL, "lb_get_populations: null argument%s");
+    const long long N = h->nodes;
+    lb_status st = ensure_hstage(h, (size_t)N * 9 * sizeof(double));
+    if (st != LB_OK) return st;
+    long long maxn = 0;
+    for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
+    dim3 g(grid_for(maxn), h->n_ch);
+    double* s = (double*)h->hstage;
+    switch (h->prec) {
+        case LB_PREC_F64: k_pop_to_f64<double, double><<<g, 256, 0, h->stream>>>((const double*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
+        case LB_PREC_F32: k_pop_to_f64<float, float><<<g, 256, 0, h->stream>>>((const float*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
+        default: k_pop_to_f64<__nv_bfloat16, float><<<g, 256, 0, h->stream>>>((const __nv_bfloat16*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
+    }
+    LB_CK(cudaGetLastError());
+    LB_CK(cudaMemcpyAsync(n, s, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    if (h->csize == 8) k_planes_to_f64<double><<<g, 256, 0, h->stream>>>((const double*)h->drho, s, 1, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+    else k_planes_to_f64<float><<<g, 256, 0, h->stream>>>((const float*)h->drho, s, 1, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+    LB_CK(cudaGetLastError());
+    LB_CK(cudaMemcpyAsync(drho, s, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    if (sig3 && h->smode == 1) {
+        if (h->csize == 8) k_planes_to_f64<double><<<g, 256, 0, h->stream>>>((const double*)h->sig3, s, 3, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+        else k_planes_to_f64<float><<<g, 256, 0, h->stream>>>((const float*)h->sig3, s, 3, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+        LB_CK(cudaGetLastError());
+        LB_CK(cudaMemcpyAsync(sig3, s, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        LB_CK(cudaStreamSynchronize(h->stream));
+    }
+    return LB_OK;
+}
+
+namespace {
+struct StateHeader {
+    uint64_t magic, version;
+    int64_t step, planes;
+    int32_t n_ch, nx, prec, smode;
+};
+constexpr uint64_t kMagic = 0x4d4c4e2d424c6772ull;
+}  // namespace
+
+size_t lb_state_bytes(const lb_handle* h) {
+    if (!h) return 0;
+    size_t b = sizeof(StateHeader) + 9 * h->planes * h->tsize + h->planes * h->csize;
+    if (h->smode == 1) b += 3 * h->planes * h->csize;
+    return b;
+}
+
+lb_status lb_get_state(lb_handle* h, void* buf, size_t bytes) {
+    if (!h || !buf || bytes < lb_state_bytes(h)) return fail(LB_EINVAL, "lb_get_state: bad buffer%s");
+    StateHeader hd{kMagic, 1, h->step, h->planes, h->n_ch, h->nx, h->prec, h->smode};
+    char* p = (char*)buf;
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    LB_CK(cudaMemcpyAsync(p, h->popA, 9 * h->planes * h->tsize, cudaMemcpyDeviceToHost, h->stream));
+    p += 9 * h->planes * h->tsize;
+    LB_CK(cudaMemcpyAsync(p, h->drho, h->planes * h->csize, cudaMemcpyDeviceToHost, h->stream));
+    p += h->planes * h->csize;
+    if (h->smode == 1) LB_CK(cudaMemcpyAsync(p, h->sig3, 3 * h->planes * h->csize, cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+lb_status lb_set_state(lb_handle* h, const void* buf, size_t bytes) {
+    if (!h || !buf || bytes < lb_state_bytes(h)) return fail(LB_EINVAL, "lb_set_state: bad buffer%s");
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kMagic || hd.planes != h->planes || hd.n_ch != h->n_ch || hd.nx != h->nx || hd.prec != h->prec ||
+        hd.smode != h->smode)
+        return fail(LB_EINVAL, "lb_set_state: image does not match this handle's grid%s");
+    const char* p = (const char*)buf + sizeof hd;
+    LB_CK(cudaMemcpyAsync(h->popA, p, 9 * h->planes * h->tsize, cudaMemcpyHostToDevice, h->stream));
+    p += 9 * h->planes * h->tsize;
+    LB_CK(cudaMemcpyAsync(h->drho, p, h->planes * h->csize, cudaMemcpyHostToDevice, h->stream));
+    p += h->planes * h->csize;
+    if (h->smode == 1) LB_CK(cudaMemcpyAsync(h->sig3, p, 3 * h->planes * h->csize, cudaMemcpyHostToDevice, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    h->step = hd.step;
+    h->uprev_state = -10;
+    h->mon_state = -1;
+    return LB_OK;
+}
+
+lb_status lb_channel_status(lb_handle* h, int* status) {
+    if (!h || !status) return fail(LB_EINVAL, "lb_channel_status: null argument%s");
+    LB_CK(cudaMemcpyAsync(status, h->status_d, sizeof(int) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < h->n_ch; ++c)
+        if (status[c]) h->any_unstable = true;
+    return LB_OK;
+}
+
+}  // extern "C"

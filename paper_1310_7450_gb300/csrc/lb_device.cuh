@@ -1,0 +1,213 @@
+// lb_device.cuh -- device-side types and the per-node arithmetic of the nlM lattice-Boltzmann
+// step (Papenkort & Voigtmann, arXiv:1310.7450, Sec. II and III A).
+//
+// Storage: populations are kept as deviations d_i = n_i - w_i from the rest equilibrium at unit
+// density (FP64, FP32 or BF16); all arithmetic below works on deviations so that FP32 keeps the
+// precision of the small quantities (sum_i w_i = 1 and sum_i c_i w_i = 0 make this exact).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbk {
+
+// D2Q9 velocity set (Sec. II A).  Numbering: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1)
+// 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i == 1 ? 3 : (i == 2 ? 4 : (i == 3 ? 1 : (i == 4 ? 2 : (i == 5 ? 7 : (i == 6 ? 8 : (i == 7 ? 5 : 6)))))));
+}
+// lattice weights a^{c_i}: 4/9, 1/9, 1/36
+template <typename C>
+__host__ __device__ constexpr C wgt(int i) {
+    return i == 0 ? C(4) / C(9) : (i < 5 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// ---- storage precision ---------------------------------------------------------------------
+template <typename T> struct Store;
+template <> struct Store<double> {
+    using C = double;
+    static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct Store<__nv_bfloat16> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---- launch descriptors ----------------------------------------------------------------------
+// Per-channel constants, precomputed on the host in the arithmetic type C.
+template <typename C>
+struct ChanParams {
+    long long base;      // plane offset: channel planes start at k*base (k planes per field)
+    long long P;         // plane stride (elements), >= nx*ny, padded
+    long long node_off;  // compact node offset of the channel (field outputs)
+    int ny;
+    int pad_;
+    C omega;    // 1/tau_LB (BGK)
+    C k1;       // -1/(2 c_s^4 tau_LB) = -9/(2 tau_LB): traceless-stress line of Eq. (bodyforce)
+    C k2;       // 1 - 1/(2 tau_LB)
+    C gx;       // body force density f^ex_x
+    C G;        // G_inf
+    C tau;      // theta * tau0
+    C inv_gc;   // 1/gamma_c (0 = no shear thinning)
+    C cD;       // eta_inf - eta^N = G tau0 - rho0 (tau_LB - 1/2)/3: Sigma^nN = sigma + cD D
+};
+
+struct WorkItem {
+    int ch;   // channel
+    int x0;   // first column
+    int nxt;  // columns (== nx: full-width tile, x wraps inside the tile)
+    int y0;   // first row
+    int nyt;  // rows (>= 2, or the whole channel)
+    int pad_[3];
+};
+
+enum : int {
+    F_FIELDS = 1,       // compute the fields of the state only (no population/state writes)
+    F_STORE_SIGMA = 2,  // write sigma (xx, yy, zz, xy) planes this step
+    F_SAVE_U = 4,       // write the reported velocity into the u_prev planes
+    F_RESID = 8,        // accumulate the residual against u_prev (block partials)
+};
+
+template <typename T, typename C>
+struct StepArgs {
+    const T* __restrict__ pin;     // populations of the stored state (deviations)
+    T* __restrict__ pout;          // populations after this step
+    C* __restrict__ drho;          // delta rho of the last collision [plane]
+    C* __restrict__ sig3;          // carried stress (xx, xy, yy) [3 planes], stress mode 1
+    C* __restrict__ sig4;          // stress output (xx, yy, zz, xy) [4 planes]
+    C* __restrict__ uprev;         // saved velocity [2 planes]
+    C* __restrict__ fu;            // fields-only outputs, compact node order: u [node][2]
+    C* __restrict__ fsig;          //   sigma [node][4]
+    C* __restrict__ frho;          //   rho [node]
+    double* __restrict__ partials; // residual partials [item][4]
+    const WorkItem* __restrict__ items;
+    const ChanParams<C>* __restrict__ chan;
+    int* __restrict__ status;      // per channel: 0 stable, 1 unstable
+    int nx;
+    int flags;
+    C guard;                       // |u| above which a channel is declared unstable
+};
+
+// ---- per-node arithmetic -------------------------------------------------------------------
+
+// Moments of Eq. (rhoj) from the post-streaming deviations: dR = sum_i n_i - 1, J0 = sum c_i n_i.
+template <typename C>
+__device__ __forceinline__ void moments(const C (&d)[9], C& dR, C& jx, C& jy) {
+    dR = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+}
+
+// Velocity used for the gradients (reading: j / R0 with R0 = sum_i n_i after streaming, because
+// the density of Eq. (rhoj) needs S, which needs sigma(kappa)); one routine for the own node and
+// the halo ring so that both give bit-identical values.
+template <typename C>
+__device__ __forceinline__ void gradient_velocity(const C (&d)[9], C gx, C& dR, C& jx, C& jy, C& ux, C& uy) {
+    moments<C>(d, dR, jx, jy);
+    jx = jx + C(0.5) * gx;  // j = sum c n + f dt/2 (Eq. rhoj)
+    const C inv = C(1) / (C(1) + dR);
+    ux = jx * inv;
+    uy = jy * inv;
+}
+
+// Polymer stress sigma = (xx, xy, yy) solving  s - alpha (kappa s + s kappa^T) = b  in closed
+// form (Cramer's rule on the 3x3 system).  kappa = [[a, b], [c, e]] with kappa_ab = d_b u_a.
+// Mode 0 (Eq. sigtsum, summed): alpha = tau_M, rhs = G tau_M D.  Mode 1 (backward Euler of
+// Eq. gkder): alpha = tau_M/(tau_M+1), rhs = tau_M/(tau_M+1) (sigma_old + G D).
+// det = (1 - alpha tr kappa)((1-2 alpha a)(1-2 alpha e) - 4 alpha^2 b c) is the product of
+// 1 - alpha (lambda_i + lambda_j) over the eigenvalue pairs of kappa.
+template <typename C>
+__device__ __forceinline__ void convected_solve(C ka, C kb, C kc, C ke, C alpha, C b1, C b2, C b3,
+                                                C& sxx, C& sxy, C& syy) {
+    const C A = C(1) - C(2) * alpha * ka;
+    const C E = C(1) - C(2) * alpha * ke;
+    const C Pp = C(1) - alpha * (ka + ke);
+    const C q = alpha * alpha * kb * kc;
+    const C inv_det = C(1) / (Pp * (A * E - C(4) * q));
+    sxy = (alpha * kc * E * b1 + A * E * b2 + alpha * kb * A * b3) * inv_det;
+    sxx = ((Pp * E - C(2) * q) * b1 + C(2) * alpha * kb * E * b2 + C(2) * alpha * alpha * kb * kb * b3) * inv_det;
+    syy = (C(2) * alpha * alpha * kc * kc * b1 + C(2) * alpha * kc * A * b2 + (A * Pp - C(2) * q) * b3) * inv_det;
+}
+
+template <typename C> __device__ __forceinline__ C csqrt(C v);
+template <> __device__ __forceinline__ double csqrt<double>(double v) { return sqrt(v); }
+template <> __device__ __forceinline__ float csqrt<float>(float v) { return sqrtf(v); }
+
+// Everything between the moments and the collision for one node (Sec. II A and III A):
+// kappa -> tau_M (Eq. nlmaxwell) -> sigma -> Sigma^nN -> delta rho, S (Eq. rhoplus) ->
+// rho_eq, u (reading: sum n^eq = sum (n*+n)/2 = R0 + S/2, so that sum (Delta + F) = S).
+template <typename C>
+struct NodeState {
+    C sxx, sxy, syy;   // polymer stress
+    C Bxx, Bxy;        // traceless Sigma^nN (Byy = -Bxx)
+    C drho, S;         // delta rho(t), S = delta rho(t) - delta rho(t-1)
+    C dReq;            // rho_eq - 1
+    C ux, uy;          // velocity handed to n^eq and F_i: j / rho_eq
+};
+
+template <typename C, int SMODE>
+__device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C ka, C kb, C kc, C ke,
+                                                     C dR, C jx, C jy, C drho_prev,
+                                                     C s_old_xx, C s_old_xy, C s_old_yy) {
+    NodeState<C> r;
+    const C Dxx = C(2) * ka, Dxy = kb + kc, Dyy = C(2) * ke;
+    const C II = C(0.5) * (Dxx * Dxx + C(2) * Dxy * Dxy + Dyy * Dyy);  // (1/2) tr D^2
+    C tau_M = C(0);
+    if (P.tau > C(0)) tau_M = P.tau / (C(1) + P.tau * csqrt<C>(II) * P.inv_gc);
+    if (tau_M > C(0)) {
+        if (SMODE == 0) {
+            const C gt = P.G * tau_M;
+            convected_solve<C>(ka, kb, kc, ke, tau_M, gt * Dxx, gt * Dxy, gt * Dyy, r.sxx, r.sxy, r.syy);
+        } else {
+            const C pre = tau_M / (tau_M + C(1));
+            convected_solve<C>(ka, kb, kc, ke, pre, pre * (s_old_xx + P.G * Dxx), pre * (s_old_xy + P.G * Dxy),
+                               pre * (s_old_yy + P.G * Dyy), r.sxx, r.sxy, r.syy);
+        }
+    } else {
+        r.sxx = r.sxy = r.syy = C(0);
+    }
+    const C Nxx = r.sxx + P.cD * Dxx;
+    const C Nxy = r.sxy + P.cD * Dxy;
+    const C Nyy = r.syy + P.cD * Dyy;
+    const C T = Nxx + Nyy;
+    r.drho = C(-1.5) * T;             // -tr Sigma^nN / (c_s^2 d), d = 2
+    r.S = r.drho - drho_prev;         // dt d_t delta rho (Eq. rhoplus)
+    r.Bxx = C(0.5) * (Nxx - Nyy);
+    r.Bxy = Nxy;
+    r.dReq = dR + C(0.5) * r.S;
+    const C inv = C(1) / (C(1) + r.dReq);
+    r.ux = jx * inv;
+    r.uy = jy * inv;
+    return r;
+}
+
+// Equilibrium (Eq. neq) minus w_i, forcing term (Eq. bodyforce) and BGK, direction i.
+template <typename C, int I>
+__device__ __forceinline__ C collide_dir(const ChanParams<C>& P, const NodeState<C>& s, C di, C usq,
+                                         C Yxx, C Yyy, C Yxy) {
+    constexpr int X = cx(I), Y = cy(I);
+    const C w = wgt<C>(I);
+    const C cu = C(X) * s.ux + C(Y) * s.uy;
+    const C neq_dev = w * (s.dReq + (C(1) + s.dReq) * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * usq));
+    // Sigma-bar : Q_i with Byy = -Bxx;  Y : Q_i with Q_i = c_i c_i - 1/3
+    const C qs = s.Bxx * C(X * X - Y * Y) + C(2 * X * Y) * s.Bxy;
+    const C qy = Yxx * (C(X * X) - C(1) / C(3)) + Yyy * (C(Y * Y) - C(1) / C(3)) + C(2 * X * Y) * Yxy;
+    const C F = w * (P.k1 * qs + P.k2 * (s.S + C(3) * C(X) * P.gx + C(4.5) * qy));
+    return di - P.omega * (di - neq_dev) + F;
+}
+
+}  // namespace lbk

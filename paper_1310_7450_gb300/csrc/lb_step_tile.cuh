@@ -1,0 +1,237 @@
+// lb_step_tile.cuh -- the fused lattice-Boltzmann step over a 2-D tile of one channel.
+//
+// One CTA owns a tile (x0..x0+nxt-1, y0..y0+nyt-1) of one channel; one thread owns one node.
+//   phase 1  pull-stream the 9 populations of the own node (Eq. lbupdate, pull form; half-way
+//            bounce-back where the source lies beyond a wall, Sec. II B) and keep them in
+//            registers; moments (Eq. rhoj) -> gradient velocity j/R0 into shared memory;
+//   phase 2  the same moments for the one-node halo ring around the tile (recomputed from a
+//            second ring of pulled sources, so the velocity gradient uses same-time neighbours);
+//   phase 3  kappa by three-point differences from shared memory (central; one-sided second
+//            order on the first/last fluid row), the nlM stress, Sigma^nN, delta rho, n^eq, F_i
+//            and the BGK collision; store n*, delta rho, optional stress / velocity / residual.
+// A full-width tile (nxt == nx) wraps x inside the tile and needs no x halo.
+#pragma once
+
+#include "lb_device.cuh"
+
+namespace lbk {
+
+template <typename T, typename C>
+__device__ __forceinline__ void pull9(const T* __restrict__ pc, long long P, int nx, int ny, int x, int y,
+                                      C (&d)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ys = y - cy(i);
+        if (ys < 0 || ys >= ny) {
+            d[i] = Store<T>::ld(pc + (long long)opp(i) * P + (long long)y * nx + x);
+        } else {
+            int xs = x - cx(i);
+            xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+            d[i] = Store<T>::ld(pc + (long long)i * P + (long long)ys * nx + xs);
+        }
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ C warp_sum(C v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename C>
+__device__ __forceinline__ C warp_max(C v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block size: NT threads; tile nxt*nyt <= NT.
+template <typename T, typename C, int SMODE, int NT>
+__global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* su = reinterpret_cast<C*>(smem_raw);  // [EY*EX][2] gradient velocity
+
+    const WorkItem it = a.items[blockIdx.x];
+    if (a.status[it.ch] != 0) return;  // retired channel (uniform for the CTA)
+    const ChanParams<C> P = a.chan[it.ch];
+    const int nx = a.nx, ny = P.ny;
+    const bool full = (it.nxt == nx);
+    const int EX = full ? nx : it.nxt + 2;
+    const int ex0 = full ? 0 : 1;
+    const int EY = it.nyt + 2;
+    const int t = threadIdx.x;
+    const int ntile = it.nxt * it.nyt;
+    const T* pc = a.pin + 9 * P.base;
+
+    // phase 1: own node
+    const bool own = t < ntile;
+    const int tx = own ? t % it.nxt : 0;
+    const int ty = own ? t / it.nxt : 0;
+    const int x = it.x0 + tx, y = it.y0 + ty;
+    C d[9];
+    C dR = C(0), jx = C(0), jy = C(0);
+    if (own) {
+        pull9<T, C>(pc, P.P, nx, ny, x, y, d);
+        C ux, uy;
+        gradient_velocity<C>(d, P.gx, dR, jx, jy, ux, uy);
+        const int e = (ty + 1) * EX + (tx + ex0);
+        su[2 * e] = ux;
+        su[2 * e + 1] = uy;
+    }
+    // phase 2: halo ring (rows y0-1 and y0+nyt; columns x0-1 and x0+nxt for split tiles)
+    const int R = 2 * EX + (full ? 0 : 2 * it.nyt);
+    for (int r = t; r < R; r += NT) {
+        int ex, ey;
+        if (r < EX) { ex = r; ey = 0; }
+        else if (r < 2 * EX) { ex = r - EX; ey = EY - 1; }
+        else { const int k = r - 2 * EX; ey = 1 + (k >> 1); ex = (k & 1) ? EX - 1 : 0; }
+        const int hy = it.y0 - 1 + ey;
+        C ux = C(0), uy = C(0);
+        if (hy >= 0 && hy < ny) {
+            int hx = full ? ex : it.x0 - 1 + ex;
+            hx = hx < 0 ? hx + nx : (hx >= nx ? hx - nx : hx);
+            C dh[9], hR, hjx, hjy;
+            pull9<T, C>(pc, P.P, nx, ny, hx, hy, dh);
+            gradient_velocity<C>(dh, P.gx, hR, hjx, hjy, ux, uy);
+        }
+        const int e = ey * EX + ex;
+        su[2 * e] = ux;
+        su[2 * e + 1] = uy;
+    }
+    __syncthreads();
+
+    C res_du2 = C(0), res_u2 = C(0), res_ux = C(0), res_umax = C(0);
+    if (own) {
+        // phase 3: velocity gradient kappa_ab = d_b u_a (three-point differences)
+        const int ecx = tx + ex0, ecy = ty + 1;
+        int exm, exp_;
+        if (full) { exm = ecx == 0 ? EX - 1 : ecx - 1; exp_ = ecx == EX - 1 ? 0 : ecx + 1; }
+        else { exm = ecx - 1; exp_ = ecx + 1; }
+        const C* rowc = su + 2 * (ecy * EX);
+        const C ka = C(0.5) * (rowc[2 * exp_] - rowc[2 * exm]);          // d_x u_x
+        const C kc = C(0.5) * (rowc[2 * exp_ + 1] - rowc[2 * exm + 1]);  // d_x u_y
+        C kb, ke;
+        if (y == 0) {
+            const C* r1 = su + 2 * ((ecy + 1) * EX + ecx);
+            const C* r2 = su + 2 * ((ecy + 2) * EX + ecx);
+            const C* r0 = su + 2 * (ecy * EX + ecx);
+            kb = C(0.5) * (C(-3) * r0[0] + C(4) * r1[0] - r2[0]);
+            ke = C(0.5) * (C(-3) * r0[1] + C(4) * r1[1] - r2[1]);
+        } else if (y == ny - 1) {
+            const C* r1 = su + 2 * ((ecy - 1) * EX + ecx);
+            const C* r2 = su + 2 * ((ecy - 2) * EX + ecx);
+            const C* r0 = su + 2 * (ecy * EX + ecx);
+            kb = C(0.5) * (C(3) * r0[0] - C(4) * r1[0] + r2[0]);
+            ke = C(0.5) * (C(3) * r0[1] - C(4) * r1[1] + r2[1]);
+        } else {
+            const C* rp = su + 2 * ((ecy + 1) * EX + ecx);
+            const C* rm = su + 2 * ((ecy - 1) * EX + ecx);
+            kb = C(0.5) * (rp[0] - rm[0]);
+            ke = C(0.5) * (rp[1] - rm[1]);
+        }
+        const long long pn = (long long)y * nx + x;  // node inside the channel planes
+        C* dr = a.drho + P.base;
+        const C drho_prev = dr[pn];
+        C so_xx = C(0), so_xy = C(0), so_yy = C(0);
+        if (SMODE == 1) {
+            const C* s3 = a.sig3 + 3 * P.base;
+            so_xx = s3[pn];
+            so_xy = s3[P.P + pn];
+            so_yy = s3[2 * P.P + pn];
+        }
+        const NodeState<C> s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dR, jx, jy, drho_prev, so_xx, so_xy, so_yy);
+
+        // reported fields: hydrodynamic density rho_eq - delta rho (Eq. rhoj), u = j / rho
+        const C rho_h = C(1) + s.dReq - s.drho;
+        const C urx = jx / rho_h, ury = jy / rho_h;
+        const C umag = csqrt<C>(urx * urx + ury * ury);
+        if (!(umag <= a.guard)) atomicOr(a.status + it.ch, 1);  // NaN or too fast
+
+        if (a.flags & F_FIELDS) {
+            const long long node = P.node_off + pn;
+            a.fu[2 * node] = urx;
+            a.fu[2 * node + 1] = ury;
+            a.fsig[4 * node + 0] = s.sxx;
+            a.fsig[4 * node + 1] = s.syy;
+            a.fsig[4 * node + 2] = C(0);
+            a.fsig[4 * node + 3] = s.sxy;
+            a.frho[node] = rho_h;
+        } else {
+            const C usq = s.ux * s.ux + s.uy * s.uy;
+            // the tensor multiplying Q_i in Eq. (bodyforce): -S u u + u f + f u, f = (gx, 0)
+            const C Yxx = -s.S * s.ux * s.ux + C(2) * s.ux * P.gx;
+            const C Yyy = -s.S * s.uy * s.uy;
+            const C Yxy = -s.S * s.ux * s.uy + s.uy * P.gx;
+            T* po = a.pout + 9 * P.base + pn;
+            Store<T>::st(po + 0 * P.P, collide_dir<C, 0>(P, s, d[0], usq, Yxx, Yyy, Yxy));
+            Store<T>::st(po + 1 * P.P, collide_dir<C, 1>(P, s, d[1], usq, Yxx, Yyy, Yxy));
+            Store<T>::st(po + 2 * P.P, collide_dir<C, 2>(P, s, d[2], usq, Yxx, Yyy, Yxy));
+            Store<T>::st(po + 3 * P.P, collide_dir<C, 3>(P, s, d[3], usq, Yxx, Yyy, Yxy));
+            Store<T>::st(po + 4 * P.P, collide_dir<C, 4>(P, s, d[4], usq, Yxx, Yyy, Yxy));
+            Store<T>::st(po + 5 * P.P, collide_dir<C, 5>(P, s, d[5], usq, Yxx, Yyy, Yxy));
+            Store<T>::st(po + 6 * P.P, collide_dir<C, 6>(P, s, d[6], usq, Yxx, Yyy, Yxy));
+            Store<T>::st(po + 7 * P.P, collide_dir<C, 7>(P, s, d[7], usq, Yxx, Yyy, Yxy));
+            Store<T>::st(po + 8 * P.P, collide_dir<C, 8>(P, s, d[8], usq, Yxx, Yyy, Yxy));
+            dr[pn] = s.drho;
+            if (SMODE == 1) {
+                C* s3 = a.sig3 + 3 * P.base;
+                s3[pn] = s.sxx;
+                s3[P.P + pn] = s.sxy;
+                s3[2 * P.P + pn] = s.syy;
+            }
+            if (a.flags & F_STORE_SIGMA) {
+                C* s4 = a.sig4 + 4 * P.base;
+                s4[pn] = s.sxx;
+                s4[P.P + pn] = s.syy;
+                s4[2 * P.P + pn] = C(0);
+                s4[3 * P.P + pn] = s.sxy;
+            }
+        }
+        if (a.flags & (F_RESID | F_SAVE_U)) {
+            C* up = a.uprev + 2 * P.base;
+            if (a.flags & F_RESID) {
+                const C dx_ = urx - up[pn], dy_ = ury - up[P.P + pn];
+                res_du2 = dx_ * dx_ + dy_ * dy_;
+                res_u2 = urx * urx + ury * ury;
+                res_ux = urx;
+                res_umax = umag;
+            }
+            if (a.flags & F_SAVE_U) {
+                up[pn] = urx;
+                up[P.P + pn] = ury;
+            }
+        }
+    }
+    if (a.flags & F_RESID) {
+        // block reduction of (sum du^2, sum u^2, sum u_x, max |u|) in double
+        __shared__ double red[NT / 32][4];
+        double v0 = warp_sum<double>((double)res_du2), v1 = warp_sum<double>((double)res_u2);
+        double v2 = warp_sum<double>((double)res_ux), v3 = warp_max<double>((double)res_umax);
+        const int w = t >> 5, l = t & 31;
+        if (l == 0) { red[w][0] = v0; red[w][1] = v1; red[w][2] = v2; red[w][3] = v3; }
+        __syncthreads();
+        if (t == 0) {
+            double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            for (int k = 0; k < NT / 32; ++k) { s0 += red[k][0]; s1 += red[k][1]; s2 += red[k][2]; s3 = fmax(s3, red[k][3]); }
+            double* o = a.partials + 4 * (long long)blockIdx.x;
+            o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3;
+        }
+    }
+}
+
+}  // namespace lbk
+
+namespace lbk {
+// Host-side launcher, explicitly instantiated per storage type in lb_kernels_*.cu.
+template <typename T, typename C, int SMODE>
+cudaError_t launch_step_tile(const StepArgs<T, C>& a, int n_items, size_t smem, cudaStream_t s) {
+    constexpr int NT = 256;
+    auto k = k_step_tile<T, C, SMODE, NT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (n_items > 0) k<<<n_items, NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace lbk

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every function include/lbnlm.h declares; argument
+validation that happens before any CUDA call is exercised on the CPU."""
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1310_7450_gb300 import build, lbnlm
+    build.build()
+    return lbnlm.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lbnlm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["lb_create", "lb_step", "lb_get_fields", "lb_residual", "lb_destroy"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_function(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror(lib):
+    from paper_1310_7450_gb300 import lbnlm
+    assert lbnlm.lb_strerror(lbnlm.LB_OK) == "ok"
+    assert "unstable" in lbnlm.lb_strerror(lbnlm.LB_EUNSTABLE)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(ny=2), dict(nx=0), dict(tau_lb=0.5), dict(tau_lb=float("nan")), dict(gamma_c=0.0),
+    dict(rho0=0.0), dict(rho_pert_amp=1.0), dict(G_inf=-1.0), dict(precision=7), dict(stress_mode=3),
+])
+def test_invalid_arguments_rejected_before_any_device_work(lib, bad):
+    from paper_1310_7450_gb300 import lbnlm
+    p = dict(tau_lb=0.9, g_x=1e-6, G_inf=1e-3, tau0=1.0, theta=10.0, gamma_c=0.1, rho0=1.0)
+    kw = dict(nx=4, ny=16, precision=0, stress_mode=0)
+    for k, v in bad.items():
+        if k in kw:
+            kw[k] = v
+        else:
+            p[k] = v
+    with pytest.raises(lbnlm.LBError) as e:
+        lbnlm.lb_create(kw["nx"], kw["ny"], p, kw["precision"], kw["stress_mode"])
+    assert e.value.status == lbnlm.LB_EINVAL
+    assert lbnlm.lb_last_error()
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_1310_7450_gb300 import lbnlm
+    assert lib.lb_step(None, 1) == lbnlm.LB_EINVAL
+    assert lib.lb_step_count(None) == -1
+    assert lib.lb_num_nodes(None) == 0
+    lib.lb_destroy(None)

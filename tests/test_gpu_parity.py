@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative, infinity norm of the difference over the infinity norm of the oracle field):
+FP64 storage 1e-12, FP32 storage 1e-5 on u and sigma.  Grids span several tiles and ragged tails
+(tiles are 32 x 8 for nx > 128, full width with 256/nx rows otherwise) and the degenerate
+widths nx = 1, 2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_7450_gb300 import inputs, lbnlm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+def rel(a, b):
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def random_state(nx, ny, seed, amp=1e-2):
+    rng = np.random.default_rng(seed)
+    st = oracle.init_state(1.0 + amp * rng.uniform(-1, 1, (ny, nx)))
+    w = oracle.equilibrium(1.0, 0.0, 0.0)
+    st.nstar += amp * rng.uniform(-1, 1, st.nstar.shape) * w[:, None, None]
+    st.drho[:] = 1e-2 * amp * rng.uniform(-1, 1, (ny, nx))
+    return st
+
+
+def nlm(theta=10.0, g=1e-5, G=1e-3):
+    return inputs.matched_params(0.9, theta, 0.1, G, g)
+
+
+GRIDS = [(4, 200), (40, 13), (70, 29), (1, 10), (2, 3), (128, 5), (129, 7), (33, 17)]
+
+
+@pytest.mark.parametrize("nx,ny", GRIDS)
+def test_fp64_random_state_matches_oracle(stream, nx, ny):
+    p = nlm()
+    st = random_state(nx, ny, 1000 + nx * 7 + ny)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream) as sim:
+        sim.set_populations([st.nstar], [st.drho])
+        sim.step(30)
+        (n_g, d_g), = sim.populations()
+        (u_g, s_g, r_g), = sim.fields()
+    oracle.run(p, st, 30)
+    u_o, s_o, r_o = oracle.fields(p, st)
+    w = oracle.equilibrium(1.0, 0.0, 0.0)[:, None, None]
+    assert rel(n_g - w, st.nstar - w) < 1e-12
+    assert rel(d_g, st.drho) < 1e-11
+    assert rel(u_g, u_o) < 1e-12
+    assert rel(s_g, s_o) < 1e-11
+    assert rel(r_g - 1, r_o - 1) < 1e-11
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp64_yield_stress_channel_20000_steps(stream, mode):
+    """4 x 64 channel, theta = 100, tau = 1e4, gamma_c = 0.1, wp H = 1/2, from rest: 20000 steps."""
+    cfg = inputs.oracle_channel_yield()
+    p = dict(cfg["params"], stress_mode=mode)
+    nx, ny, steps = cfg["nx"], cfg["ny"], cfg["steps"]
+    with lbnlm.Channels(nx, ny, p, "f64", stress_mode=mode, stream=stream) as sim:
+        sim.step(steps)
+        (u_g, s_g, r_g), = sim.fields()
+    st = oracle.init_state(np.ones((ny, nx)))
+    oracle.run(p, st, steps)
+    u_o, s_o, r_o = oracle.fields(p, st)
+    assert rel(u_g, u_o) < 1e-12
+    assert rel(s_g, s_o) < 1e-12
+    assert np.abs(u_o).max() > 1e-3  # the flow is well developed
+
+
+def test_fp64_newtonian_channel(stream):
+    cfg = inputs.oracle_channel_newtonian()
+    p, nx, ny, steps = cfg["params"], cfg["nx"], cfg["ny"], cfg["steps"]
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream) as sim:
+        sim.step(steps)
+        (u_g, _, _), = sim.fields()
+    st = oracle.init_state(np.ones((ny, nx)))
+    oracle.run(p, st, steps)
+    u_o, _, _ = oracle.fields(p, st)
+    assert rel(u_g, u_o) < 1e-12
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp32_yield_stress_channel(stream, mode):
+    cfg = inputs.oracle_channel_yield()
+    p = dict(cfg["params"], stress_mode=mode)
+    nx, ny, steps = cfg["nx"], cfg["ny"], cfg["steps"]
+    with lbnlm.Channels(nx, ny, p, "f32", stress_mode=mode, stream=stream) as sim:
+        sim.step(steps)
+        (u_g, s_g, _), = sim.fields()
+    st = oracle.init_state(np.ones((ny, nx)))
+    oracle.run(p, st, steps)
+    u_o, s_o, _ = oracle.fields(p, st)
+    assert rel(u_g, u_o) < 1e-5
+    assert rel(s_g, s_o) < 1e-5
+
+
+@pytest.mark.parametrize("nx,ny", [(40, 13), (129, 7), (4, 200)])
+def test_fp32_random_state(stream, nx, ny):
+    p = nlm()
+    st = random_state(nx, ny, 77 + nx + ny)
+    with lbnlm.Channels(nx, ny, p, "f32", stream=stream) as sim:
+        sim.set_populations([st.nstar], [st.drho])
+        sim.step(30)
+        (u_g, s_g, _), = sim.fields()
+    oracle.run(p, st, 30)
+    u_o, s_o, _ = oracle.fields(p, st)
+    assert rel(u_g, u_o) < 1e-5
+    assert rel(s_g, s_o) < 1e-4  # sigma of random states is dominated by FD of FP32 noise
+
+
+def test_seeded_initial_density_matches_input_generator(stream):
+    nx, ny = 37, 11
+    p = dict(nlm(), rho_pert_amp=1e-3, seed=12345)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream) as sim:
+        (n_g, d_g), = sim.populations()
+    rho = inputs.initial_density(nx, ny, 1.0, 1e-3, 12345)
+    assert np.abs(n_g.sum(axis=0) - rho).max() < 1e-15
+    assert np.all(d_g == 0)
+
+
+def test_batch_equals_solo_runs_bitwise(stream):
+    nys = [17, 64, 9]
+    ps = [nlm(10.0, 1e-5), nlm(100.0, 3e-6, 2e-3), nlm(0.0, 1e-6)]
+    ps = [dict(q, rho_pert_amp=1e-3, seed=s) for q, s in zip(ps, [1, 2, 3])]
+    with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim:
+        sim.step(500)
+        batch = sim.populations()
+    for k, (ny, q) in enumerate(zip(nys, ps)):
+        with lbnlm.Channels(4, ny, q, "f64", stream=stream) as solo:
+            solo.step(500)
+            (n1, d1), = solo.populations()
+        assert np.array_equal(n1, batch[k][0]) and np.array_equal(d1, batch[k][1])
+
+
+def test_mass_invariant_on_gpu(stream):
+    nx, ny = 45, 23
+    p = nlm()
+    st = random_state(nx, ny, 5)
+    m0 = oracle.mass(st)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream) as sim:
+        sim.set_populations([st.nstar], [st.drho])
+        sim.step(400)
+        (n_g, d_g), = sim.populations()
+    assert abs(n_g.sum() - d_g.sum() - m0) <= 1e-13 * nx * ny
+
+
+def test_residual_flux_and_max_match_numpy(stream):
+    nx, ny = 4, 40
+    p = dict(nlm(), rho_pert_amp=1e-4, seed=3)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream) as a, lbnlm.Channels(nx, ny, p, "f64", stream=stream) as b:
+        a.step(50)
+        mon = a.monitor()[0]
+        b.step(48)
+        (u48, _, _), = b.fields()
+        b.step(1)
+        (u49, _, _), = b.fields()
+    r = np.sqrt(((u49 - u48) ** 2).sum() / (u49 ** 2).sum())
+    assert mon[0] == pytest.approx(r, rel=1e-9)
+    assert mon[1] == pytest.approx(u49[..., 0].sum() / nx, rel=1e-12)
+    assert mon[2] == pytest.approx(np.sqrt((u49 ** 2).sum(axis=-1)).max(), rel=1e-12)
+    assert mon[3] == 49
+
+
+def test_no_residual_before_two_steps(stream):
+    with lbnlm.Channels(4, 8, nlm(), "f64", stream=stream) as sim:
+        with pytest.raises(lbnlm.LBError) as e:
+            sim.monitor()
+        assert e.value.status == lbnlm.LB_ESTATE
+        sim.step(1)
+        with pytest.raises(lbnlm.LBError):
+            sim.monitor()
+        sim.step(1)  # previous call saved u: now a residual exists
+        assert np.isfinite(sim.monitor()[0, 0])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_checkpoint_resume_bitwise(stream, prec):
+    nx, ny = 33, 21
+    p = dict(nlm(), rho_pert_amp=1e-3, seed=9)
+    with lbnlm.Channels(nx, ny, p, prec, stress_mode=1, stream=stream) as a:
+        a.step(100)
+        buf = np.zeros(lbnlm.lb_state_bytes(a.h), dtype=np.uint8)
+        lbnlm.lb_get_state(a.h, buf)
+        a.step(50)
+        (na, da), = a.populations()
+        with lbnlm.Channels(nx, ny, p, prec, stress_mode=1, stream=stream) as b:
+            lbnlm.lb_set_state(b.h, buf)
+            assert lbnlm.lb_step_count(b.h) == 100
+            b.step(50)
+            (nb, db), = b.populations()
+    assert np.array_equal(na, nb) and np.array_equal(da, db)
+
+
+def test_unstable_channel_is_retired_and_others_unaffected(stream):
+    nys = [12, 12, 12]
+    ps = [dict(nlm(), rho_pert_amp=1e-3, seed=s) for s in (1, 2, 3)]
+    with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim:
+        pops = sim.populations()
+        n1 = pops[1][0].copy()
+        n1[3, 5, 2] = np.nan  # host-side fault injection into channel 1
+        sim.set_populations([pops[0][0], n1, pops[2][0]], [pops[0][1], pops[1][1], pops[2][1]])
+        st = sim.step(20)
+        status = sim.status()
+        st2 = sim.step(1)
+        after = sim.populations()
+    assert list(status) == [0, 1, 0]
+    assert lbnlm.LB_EUNSTABLE in (st, st2)
+    for k in (0, 2):
+        with lbnlm.Channels(4, 12, ps[k], "f64", stream=stream) as solo:
+            solo.step(21)
+            (ns, ds), = solo.populations()
+        assert np.array_equal(ns, after[k][0])
+
+
+def test_body_force_switch_for_cessation(stream):
+    """Setting g = 0 (cessation) through the ABI equals an oracle run with the same switch."""
+    nx, ny = 4, 32
+    p = nlm(100.0, 2e-6)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream) as sim:
+        sim.step(3000)
+        lbnlm.lb_set_body_force(sim.h, -1, 0.0)
+        sim.step(2000)
+        (u_g, s_g, _), = sim.fields()
+    st = oracle.init_state(np.ones((ny, nx)))
+    oracle.run(p, st, 3000)
+    oracle.run(dict(p, g_x=0.0), st, 2000)
+    u_o, s_o, _ = oracle.fields(dict(p, g_x=0.0), st)
+    assert rel(u_g, u_o) < 1e-12 and rel(s_g, s_o) < 1e-11
+
+
+def test_set_fields_warm_start_matches_oracle(stream):
+    from oracle import analytic
+    ny = 48
+    p = inputs.yield_stress_channel(ny, theta=10.0, tau=10.0 * 60.0)
+    ua = analytic.channel_profile(ny, p["g_x"], p["G_inf"], p["tau0"], p["theta"], p["gamma_c"])
+    nx = 3
+    u = np.zeros((ny, nx, 2))
+    u[:, :, 0] = ua[:, None]
+    rho = np.ones((ny, nx))
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream) as sim:
+        lbnlm.lb_set_fields(sim.h, u.reshape(-1), rho.reshape(-1), None)
+        sim.step(300)
+        (u_g, _, _), = sim.fields()
+    st = oracle.flow_state(rho, ua[:, None] * np.ones((1, nx)), np.zeros((ny, nx)), p["g_x"])
+    oracle.run(p, st, 300)
+    u_o, _, _ = oracle.fields(p, st)
+    assert rel(u_g, u_o) < 1e-12
+
+
+def test_fields_float32_output_and_device_output(stream):
+    import torch
+    nx, ny = 8, 16
+    p = dict(nlm(), rho_pert_amp=1e-3, seed=4)
+    with lbnlm.Channels(nx, ny, p, "f32", stream=stream) as sim:
+        sim.step(10)
+        u64 = np.zeros(2 * nx * ny)
+        lbnlm.lb_get_fields(sim.h, u64, None, None, 0, False)
+        u32 = np.zeros(2 * nx * ny, dtype=np.float32)
+        lbnlm.lb_get_fields(sim.h, u32, None, None, 1, False)
+        ud = torch.zeros(2 * nx * ny, dtype=torch.float32, device="cuda")
+        lbnlm.lb_get_fields(sim.h, ud, None, None, 1, True)
+        torch.cuda.synchronize()
+    assert np.array_equal(u32, u64.astype(np.float32))
+    assert np.array_equal(ud.cpu().numpy(), u32)
+
+
+def test_full_size_channel_x_invariance_and_parity(stream):
+    """4096 x 4096 FP32 with the stress stored every step (the benchmark's launch configuration),
+    unperturbed: every column stays bitwise identical, so any column equals the oracle's 4 x 4096
+    channel (checked at all 4096 rows after 200 steps)."""
+    nx, ny, steps = 4096, 4096, 200
+    p = inputs.single_large_channel()["params"]
+    with lbnlm.Channels(nx, ny, p, "f32", flags=lbnlm.LB_GRID_STORE_SIGMA, stream=stream) as sim:
+        sim.step(steps)
+        (u_g, s_g, _), = sim.fields()
+    for x in (1, 2047, 4095):
+        assert np.array_equal(u_g[:, x], u_g[:, 0]) and np.array_equal(s_g[:, x], s_g[:, 0])
+    st = oracle.init_state(np.ones((ny, 4)))
+    oracle.run(p, st, steps, nthreads=8)
+    u_o, s_o, _ = oracle.fields(p, st)
+    assert rel(u_g[:, :4], u_o) < 1e-5
+    assert rel(s_g[:, :4], s_o) < 1e-5
+
+
+def test_full_size_perturbed_start_matches_oracle(stream):
+    """4096 x 4096 FP32 from the seeded density perturbation (amplitude 1e-6): 3 steps, every node."""
+    cfg = inputs.single_large_channel()
+    nx, ny, steps = cfg["nx"], cfg["ny"], 3
+    p = dict(cfg["params"], rho_pert_amp=cfg["rho_pert_amp"], seed=cfg["seed"])
+    with lbnlm.Channels(nx, ny, p, "f32", flags=lbnlm.LB_GRID_STORE_SIGMA, stream=stream) as sim:
+        sim.step(steps)
+        (u_g, s_g, r_g), = sim.fields()
+    st = oracle.init_state(inputs.initial_density(nx, ny, 1.0, cfg["rho_pert_amp"], cfg["seed"]))
+    oracle.run(p, st, steps, nthreads=16)
+    u_o, s_o, r_o = oracle.fields(p, st)
+    assert rel(u_g, u_o) < 1e-5
+    assert rel(r_g - 1, r_o - 1) < 1e-4
