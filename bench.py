@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused nlM lattice-Boltzmann step on GB300.
+
+Workload (default): the single large channel -- 4096 x 4096 nodes, x periodic, bounce-back walls,
+FP32 SoA populations stored as deviations from the lattice weights, the 4-component polymer
+stress written every step, nlM model theta = 100, gamma_c = 0.1, tau_LB = 0.9, g = 1e-6,
+G_inf = 1e-3, start-up from rho = 1 + 1e-6 U(-1,1) (SplitMix64 seed 1).  One benchmark step is
+one lattice-Boltzmann time step over all nodes.  The state (1.6 GB) is far larger than L2.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & % HBM roofline; batched-sweep time-to-steady, plain vs warm-start"
+UNIT = "GLUPS"
+KERNEL_SOURCES = {
+    "k_step_march": ["paper_1310_7450_gb300/csrc/lb_step_march.cuh", "paper_1310_7450_gb300/csrc/lb_device.cuh"],
+    "k_step_tile": ["paper_1310_7450_gb300/csrc/lb_step_tile.cuh", "paper_1310_7450_gb300/csrc/lb_device.cuh"],
+}
+
+
+def kernel_hash(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def bytes_per_node(precision: str, store_sigma: bool, stress_mode: int) -> int:
+    """Algorithmic HBM bytes per node and step: 9 population loads + 9 stores in the storage type,
+    delta rho read + write, (+ stress write), (+ carried stress read + write in stress mode 1)."""
+    t = {"f64": 8, "f32": 4, "bf16": 2}[precision]
+    c = 8 if precision == "f64" else 4
+    b = 18 * t + 2 * c
+    if store_sigma:
+        b += 4 * c
+    if stress_mode == 1:
+        b += 6 * c
+    return b
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stored_traffic(kernel: str, precision: str, workload_nodes: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, scaled to the
+    workload by nodes, or None when missing or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{precision}_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_hash(kernel):
+        return None
+    return d["dram_bytes_per_launch"] * workload_nodes / d["nodes"]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not getattr(self, "out", ""):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args):
+    from paper_1310_7450_gb300 import inputs
+    cfg = inputs.single_large_channel(args.nx, args.ny)
+    p = dict(cfg["params"], rho_pert_amp=cfg["rho_pert_amp"], seed=cfg["seed"])
+    return cfg, p
+
+
+def cpu_oracle_rate(p, nx, ny, seconds: float, threads: int):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: a nx x ny crop with
+    the same parameters and seeded perturbation; returns (GLUPS, steps, threads)."""
+    import oracle
+    from paper_1310_7450_gb300 import inputs
+    oracle.build()
+    st = oracle.init_state(inputs.initial_density(nx, ny, 1.0, p["rho_pert_amp"], p["seed"]))
+    t0 = time.perf_counter()
+    oracle.run(p, st, 1, nthreads=threads)
+    one = max(time.perf_counter() - t0, 1e-4)
+    steps = max(2, int(seconds / one))
+    t0 = time.perf_counter()
+    oracle.run(p, st, steps, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return nx * ny * steps / dt / 1e9, steps, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cfg, p = workload(args)
+    threads = os.cpu_count() or 1
+    import oracle
+    from paper_1310_7450_gb300 import inputs
+    oracle.build()
+    cnx, cny = args.ref_crop, args.ref_crop
+    st = oracle.init_state(inputs.initial_density(cnx, cny, 1.0, p["rho_pert_amp"], p["seed"]))
+    for _ in range(args.warmup):
+        oracle.run(p, st, 1, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(p, st, 1, nthreads=threads)
+    dt = time.perf_counter() - t0
+    val = cnx * cny * args.steps / dt / 1e9
+    sample = (f"{cnx}x{cny} crop of the {cfg['nx']}x{cfg['ny']} start-up workload (same parameters and "
+              f"seeded perturbation), one oracle step per benchmark step, FP64 C oracle with {threads} OpenMP threads")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"single large channel {cfg['nx']}x{cfg['ny']} start-up (oracle on a crop)",
+                       "nx": cnx, "ny": cny},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    from paper_1310_7450_gb300 import build as libbuild
+    from paper_1310_7450_gb300 import lbnlm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    libbuild.build()
+    lbnlm.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    cfg, p = workload(args)
+    nx, ny = cfg["nx"], cfg["ny"]
+    flags = lbnlm.LB_GRID_STORE_SIGMA if args.store_sigma else 0
+    sim = lbnlm.Channels(nx, ny, p, args.precision, stress_mode=args.stress_mode, flags=flags,
+                         stream=stream.cuda_stream)
+    nodes = nx * ny
+    kernel = "k_step_march" if lbnlm.lb_uses_row_march(sim.h) else "k_step_tile"
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (includes the CUDA module load and the first residual evaluation)
+    sim.step(max(args.warmup, 3))
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    with sampler:
+        time.sleep(0.3)
+        barrier()
+        ev0.record(stream)
+        st = sim.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if st != lbnlm.LB_OK:
+        print(json.dumps({"error": f"lb_step status {st}: {lbnlm.lb_last_error()}"}), flush=True)
+        return 1
+    t_max = ms
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_step = t_max / args.steps
+    value = ws * nodes / (ms_step * 1e-3) / 1e9
+    launches = args.steps + 1  # K fused step kernels (the last one the tile kernel) + the residual reduction
+
+    # end to end through the C ABI: per step the body force goes host -> device from pinned memory
+    # (lb_set_body_force), one step runs, and the channel monitor (residual, flux, max |u|) comes
+    # back to the host (lb_monitor synchronises).
+    e2e = None
+    if args.e2e_steps > 0:
+        mon = np.zeros(4)
+        g = p["g_x"]
+        for _ in range(3):
+            lbnlm.lb_set_body_force(sim.h, -1, g)
+            sim.step(1)
+            lbnlm.lb_monitor(sim.h, mon)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            lbnlm.lb_set_body_force(sim.h, -1, g)
+            sim.step(1)
+            lbnlm.lb_monitor(sim.h, mon)
+        dt = time.perf_counter() - t0
+        e2e_t = dt
+        if ws > 1:
+            tt = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e_t = float(tt.item())
+        e2e = {"value": ws * nodes * args.e2e_steps / e2e_t / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8,
+               "d2h_bytes_per_step": 32, "steps": args.e2e_steps,
+               "call": "lb_set_body_force + lb_step(1) + lb_monitor per step"}
+    sim.close()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    peak, peak_kind = measured_peaks()
+    bpn = bytes_per_node(args.precision, args.store_sigma, args.stress_mode)
+    achieved = bpn * nodes / (ms_step * 1e-3) / 1e9
+    traffic = stored_traffic(kernel, args.precision, nodes)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "bytes_per_node": bpn, "kernel": kernel, "duration_ms": ms_step}
+    cpu = None
+    if not args.no_cpu_baseline and ws >= 1 and rank == 0 and ws == 1:
+        threads = os.cpu_count() or 1
+        val, steps, dt = cpu_oracle_rate(p, args.cpu_crop, args.cpu_crop, args.cpu_seconds, threads)
+        cpu = {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_crop}x{args.cpu_crop} crop of the same workload, {steps} steps in {dt:.1f} s, "
+                         f"FP64 C oracle, {threads} OpenMP threads"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"single large channel {nx}x{ny} start-up, nlM theta=100, gamma_c=0.1, "
+                                   f"tau_LB=0.9, g=1e-6, G_inf=1e-3; FP32 SoA deviations + 4-component stress",
+                       "nx": nx, "ny": ny, "precision": args.precision, "stress_mode": args.stress_mode,
+                       "store_sigma": bool(args.store_sigma),
+                       "l2": f"state {bpn * nodes / 2**30:.2f} GiB per step, larger than the 126 MB L2 (no flush)",
+                       "parallelism": f"{ws} independent replica(s)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": sampler.summary()}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--nx", type=int, default=4096)
+    ap.add_argument("--ny", type=int, default=4096)
+    ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "f64"])
+    ap.add_argument("--stress-mode", type=int, default=0)
+    ap.add_argument("--no-store-sigma", dest="store_sigma", action="store_false")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-crop", type=int, default=512)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-crop", type=int, default=256)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -44,13 +44,16 @@ typedef enum {
     LB_ENOMEM = 2,     /* device or host allocation failed                                  */
     LB_ECUDA = 3,      /* a CUDA call or kernel launch failed (detail in lb_last_error)       */
     LB_EUNSTABLE = 4,  /* a channel produced NaN/Inf or |u| > 0.3; it is retired (not stepped) */
-    LB_ETIMEOUT = 5,   /* a bounded device-side wait gave up                                  */
+    LB_ETIMEOUT = 5,   /* a bounded device-side wait gave up (status word bit 2)              */
     LB_ESTATE = 6      /* the call needs state that does not exist yet (e.g. no residual)     */
 } lb_status;
 
-enum { LB_PREC_F64 = 0, LB_PREC_F32 = 1, LB_PREC_BF16 = 2 };
+enum { LB_PREC_F64 = 0, LB_PREC_F32 = 1, LB_PREC_BF16 = 2, LB_PREC_F64S_F32M = 3, LB_PREC_F32S_F64M = 4 };
 enum { LB_STRESS_INLM = 0, LB_STRESS_TIMESTEPPED = 1 };
-enum { LB_GRID_STORE_SIGMA = 1 }; /* lb_grid.flags: write the 4-component stress every step */
+/* lb_grid.flags: LB_GRID_STORE_SIGMA writes the 4-component stress every step; LB_GRID_TILE_ONLY
+ * keeps every step on the general tile kernel (single wide FP32/BF16 channels otherwise use the
+ * row-march kernel for the steps that need no residual or field output). */
+enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2 };
 
 typedef struct {
     int n_channels;   /* >= 1                                                              */
@@ -58,11 +61,13 @@ typedef struct {
     const int *ny;    /* [n_channels] fluid rows per channel, each >= 3 (copied)           */
     int precision;    /* LB_PREC_F64: FP64 storage and arithmetic;
                          LB_PREC_F32: populations stored as FP32 deviations n_i - w_i, FP32 math;
-                         LB_PREC_BF16: BF16 deviations, FP32 math                           */
+                         LB_PREC_BF16: BF16 deviations, FP32 math;
+                         diagnostic mixes: LB_PREC_F64S_F32M (FP64 storage, FP32 math) and
+                         LB_PREC_F32S_F64M (FP32 storage, FP64 math) separate the two errors */
     int stress_mode;  /* LB_STRESS_INLM: instantaneous nlM stress, Eq. (sigtsum) (the paper's
                          model, Sec. III A); LB_STRESS_TIMESTEPPED: one backward-Euler step of
                          the upper-convected Maxwell equation Eq. (gkder) per LB step           */
-    int flags;        /* LB_GRID_STORE_SIGMA or 0                                          */
+    int flags;        /* LB_GRID_* bits or 0                                               */
 } lb_grid;
 
 /* Per-channel physical parameters (lattice units).  The BGK collision carries the Newtonian
@@ -116,7 +121,9 @@ lb_status lb_residual(lb_handle *h, double *r);
  * (residual, flux = sum over nodes of u_x / nx, max |u|, step index of the evaluated state). */
 lb_status lb_monitor(lb_handle *h, double *out);
 
-/* Change the body force of one channel (channel = -1: all), e.g. 0 for cessation. */
+/* Change the body force of one channel (channel = -1: all), e.g. 0 for cessation.  Stream-
+ * ordered: the force goes host -> device from pinned memory and applies to every step enqueued
+ * after this call; the call does not wait for the steps enqueued before it. */
 lb_status lb_set_body_force(lb_handle *h, int channel, double g_x);
 
 /* Warm start: set every node to the equilibrium of the given hydrodynamic density and velocity
@@ -139,10 +146,12 @@ size_t lb_state_bytes(const lb_handle *h);
 lb_status lb_get_state(lb_handle *h, void *buf, size_t bytes);
 lb_status lb_set_state(lb_handle *h, const void *buf, size_t bytes);
 
-/* Per-channel status words (host [n_channels]): 0 = stable, 1 = unstable (retired). */
+/* Per-channel status words (host [n_channels]): 0 = stable; bit 1 = unstable (NaN/Inf or
+ * |u| > 0.3; the channel is retired); bit 2 = a bounded device-side wait timed out. */
 lb_status lb_channel_status(lb_handle *h, int *status);
 
 long lb_step_count(const lb_handle *h);     /* steps taken since creation (or restored)      */
+int lb_uses_row_march(const lb_handle *h);  /* 1 if plain steps run on the row-march kernel   */
 size_t lb_num_nodes(const lb_handle *h);     /* total fluid nodes over all channels           */
 void lb_destroy(lb_handle *h);               /* synchronises the stream, frees everything     */
 const char *lb_strerror(lb_status s);

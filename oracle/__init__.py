@@ -5,9 +5,10 @@ this package.  The product library (``paper_1310_7450_gb300``) never imports it 
 code with it: the oracle is plain C (``lb_oracle.c``), compiled here with gcc, plus a NumPy
 brute-force twin (``bruteforce.py``) and the paper's closed forms (``analytic.py``).
 
-State layout used by every function here (full FP64 populations, not deviations):
-    nstar[9, ny, nx]  post-collision populations n*_i of the last step (D2Q9, numbering
-                      0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1))
+State layout used by every function here:
+    dev[9, ny, nx]    post-collision populations of the last step as offsets from the lattice
+                      weights, n*_i - w_i (D2Q9, numbering 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0)
+                      4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)); ``State.nstar`` gives n*_i
     drho[ny, nx]      flow-induced density change delta rho of the last collision (Sec. II A)
     sig[3, ny, nx]    carried polymer stress (xx, xy, yy); only stress mode 1 reads it
 
@@ -60,6 +61,7 @@ def _load():
     if _lib is None:
         lib = ctypes.CDLL(build())
         lib.orc_equilibrium.argtypes = [ctypes.c_double] * 3 + [_D]
+        lib.orc_equilibrium_offset.argtypes = [ctypes.c_double] * 3 + [_D]
         lib.orc_forcing.argtypes = [ctypes.c_double, _D, ctypes.c_double, _D, _D, _D]
         lib.orc_relaxation_time.argtypes = [ctypes.c_double] * 3
         lib.orc_relaxation_time.restype = ctypes.c_double
@@ -108,6 +110,16 @@ def equilibrium(rho: float, ux: float, uy: float) -> np.ndarray:
     return out
 
 
+def equilibrium_offset(rho_m1: float, ux: float, uy: float) -> np.ndarray:
+    """Eq. (neq) minus the weights, from rho - 1 (the form the stepping uses)."""
+    out = np.zeros(9)
+    _load().orc_equilibrium_offset(rho_m1, ux, uy, _p(out))
+    return out
+
+
+WEIGHTS = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
 def forcing(tau_lb: float, sbar, S: float, u, f) -> np.ndarray:
     """Eq. (bodyforce) for one node; sbar = traceless Sigma^nN (xx, xy, yy), S = dt d_t delta rho."""
     out = np.zeros(9)
@@ -153,7 +165,7 @@ def fallback_count() -> int:
 
 @dataclass
 class State:
-    nstar: np.ndarray  # [9, ny, nx]
+    dev: np.ndarray    # [9, ny, nx]  n*_i - w_i
     drho: np.ndarray   # [ny, nx]
     sig: np.ndarray    # [3, ny, nx]
     step: int = 0
@@ -162,8 +174,13 @@ class State:
     def shape(self):
         return self.drho.shape
 
+    @property
+    def nstar(self) -> np.ndarray:
+        """Full post-collision populations n*_i (a new array)."""
+        return self.dev + WEIGHTS[:, None, None]
+
     def copy(self) -> "State":
-        return State(self.nstar.copy(), self.drho.copy(), self.sig.copy(), self.step)
+        return State(self.dev.copy(), self.drho.copy(), self.sig.copy(), self.step)
 
 
 def init_state(rho: np.ndarray) -> State:
@@ -171,7 +188,14 @@ def init_state(rho: np.ndarray) -> State:
     rho = np.ascontiguousarray(rho, dtype=np.float64)
     ny, nx = rho.shape
     st = State(np.zeros((9, ny, nx)), np.zeros((ny, nx)), np.zeros((3, ny, nx)))
-    _load().orc_init(nx, ny, _p(rho), _p(st.nstar), _p(st.drho), _p(st.sig))
+    _load().orc_init(nx, ny, _p(rho), _p(st.dev), _p(st.drho), _p(st.sig))
+    return st
+
+
+def state_from_populations(nstar: np.ndarray, drho: np.ndarray) -> State:
+    nstar = np.asarray(nstar, dtype=np.float64)
+    st = State(np.ascontiguousarray(nstar - WEIGHTS[:, None, None]), np.ascontiguousarray(drho, dtype=np.float64),
+               np.zeros((3,) + nstar.shape[1:]))
     return st
 
 
@@ -182,7 +206,7 @@ def flow_state(rho: np.ndarray, ux: np.ndarray, uy: np.ndarray, g_x: float) -> S
     st = State(np.zeros((9, ny, nx)), np.zeros((ny, nx)), np.zeros((3, ny, nx)))
     for y in range(ny):
         for x in range(nx):
-            st.nstar[:, y, x] = equilibrium(rho[y, x], ux[y, x] - 0.5 * g_x / rho[y, x], uy[y, x])
+            st.dev[:, y, x] = equilibrium_offset(rho[y, x] - 1.0, ux[y, x] - 0.5 * g_x / rho[y, x], uy[y, x])
     return st
 
 
@@ -190,7 +214,7 @@ def run(params, st: State, nsteps: int, nthreads: int = 1) -> State:
     """Advance ``st`` in place by ``nsteps`` steps; returns it."""
     ny, nx = st.shape
     pp = to_params(params)
-    rc = _load().orc_run(ctypes.byref(pp), nx, ny, _p(st.nstar), _p(st.drho), _p(st.sig),
+    rc = _load().orc_run(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho), _p(st.sig),
                          int(nsteps), int(nthreads))
     if rc != 0:
         raise ValueError("oracle rejected the grid or parameters")
@@ -206,7 +230,7 @@ def fields(params, st: State):
     sg = np.zeros((ny, nx, 4))
     rho = np.zeros((ny, nx))
     pp = to_params(params)
-    rc = _load().orc_fields(ctypes.byref(pp), nx, ny, _p(st.nstar), _p(st.drho), _p(st.sig),
+    rc = _load().orc_fields(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho), _p(st.sig),
                             _p(u), _p(sg), _p(rho))
     if rc != 0:
         raise ValueError("oracle rejected the grid or parameters")
@@ -218,7 +242,7 @@ def intermediates(params, st: State) -> np.ndarray:
     ny, nx = st.shape
     out = np.zeros((ny, nx, 8))
     pp = to_params(params)
-    rc = _load().orc_node_intermediates(ctypes.byref(pp), nx, ny, _p(st.nstar), _p(st.drho),
+    rc = _load().orc_node_intermediates(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho),
                                         _p(st.sig), _p(out))
     if rc != 0:
         raise ValueError("oracle rejected the grid or parameters")
@@ -226,8 +250,9 @@ def intermediates(params, st: State) -> np.ndarray:
 
 
 def mass(st: State) -> float:
-    """Invariant of the scheme with periodic x and bounce-back walls: sum_r (sum_i n*_i - drho)."""
-    return float(st.nstar.sum() - st.drho.sum())
+    """Invariant of the scheme with periodic x and bounce-back walls, sum_r (sum_i n*_i - drho),
+    minus the number of nodes (sum of the offsets, to keep the precision)."""
+    return float(st.dev.sum() - st.drho.sum())
 
 
 def residual(u_now: np.ndarray, u_prev: np.ndarray) -> float:

@@ -22,6 +22,11 @@
  *   8. forcing term F_i of Eq. (bodyforce);
  *   9. BGK collision  n*_i = n_i - (n_i - n^eq_i)/tau_LB + F_i  (Sec. II A).
  *
+ * Number representation: the populations are stored as their offsets from the lattice weights,
+ * dn_i = n_i - w_i (the rest equilibrium at unit density), and every formula is evaluated on
+ * those offsets (sum_i w_i = 1 and sum_i c_i w_i = 0 make the moments exact).  The formulas are
+ * the paper's; only the FP64 rounding acts on the small part instead of on n_i ~ 0.1-0.4.
+ *
  * Readings where the paper is silent or ambiguous (each repeated at its use):
  *   - the density handed to n^eq is rho_eq = R0 + S/2 with S = drho(t) - drho(t-1), which
  *     is the only choice that satisfies the zeroth-moment condition sum_i(Delta_i + F_i) = S
@@ -113,6 +118,20 @@ void orc_equilibrium(double rho, double ux, double uy, double *neq) {
                       2.0 * ORC_CX[i] * ORC_CY[i] * ux * uy +
                       (ORC_CY[i] * ORC_CY[i] - ORC_CS2) * uy * uy;
         neq[i] = ORC_W[i] * rho * (1.0 + cu / ORC_CS2 + q_uu / (2.0 * ORC_CS2 * ORC_CS2));
+    }
+}
+
+/* Eq. (neq) as an offset from the weights: n^eq_i - w_i = w_i [(rho - 1) + rho X_i] with
+ * X_i = u.c_i/c_s^2 + Q_i:uu/(2 c_s^4); rho_m1 = rho - 1. */
+void orc_equilibrium_offset(double rho_m1, double ux, double uy, double *dneq) {
+    double rho = 1.0 + rho_m1;
+    for (int i = 0; i < 9; ++i) {
+        double cu = ORC_CX[i] * ux + ORC_CY[i] * uy;
+        double q_uu = (ORC_CX[i] * ORC_CX[i] - ORC_CS2) * ux * ux +
+                      2.0 * ORC_CX[i] * ORC_CY[i] * ux * uy +
+                      (ORC_CY[i] * ORC_CY[i] - ORC_CS2) * uy * uy;
+        double X = cu / ORC_CS2 + q_uu / (2.0 * ORC_CS2 * ORC_CS2);
+        dneq[i] = ORC_W[i] * (rho_m1 + rho * X);
     }
 }
 
@@ -264,20 +283,20 @@ int orc_stress_step(const double *kappa, double tau_M, double G, const double *s
 }
 
 /* ---------------------------------------------------------------------------------- */
-/* Whole-grid state: nstar[i][y][x] post-collision populations (full values, not
- * deviations), drho[y][x] = delta rho of the last collision, sig[3][y][x] the carried
- * polymer stress (xx, xy, yy) of stress mode 1 (unused in mode 0).                      */
+/* Whole-grid state: dn[i][y][x] = n*_i - w_i, offsets of the post-collision populations
+ * from the weights; drho[y][x] = delta rho of the last collision; sig[3][y][x] the carried
+ * polymer stress (xx, xy, yy) of stress mode 1 (unused in mode 0).                       */
 
 static long orc_fallbacks = 0; /* series -> Gaussian elimination fallbacks (logged) */
 long orc_fallback_count(void) { return orc_fallbacks; }
 void orc_reset_fallback_count(void) { orc_fallbacks = 0; }
 
-/* Initial state of reading C9: every population at rest equilibrium n_i = w_i rho(r),
- * no flow-induced density (drho = 0), no polymer stress. */
-void orc_init(int nx, int ny, const double *rho, double *nstar, double *drho, double *sig) {
+/* Initial state: every population at rest equilibrium n_i = w_i rho(r), i.e. offsets
+ * w_i (rho - 1); no flow-induced density (drho = 0), no polymer stress. */
+void orc_init(int nx, int ny, const double *rho, double *dn, double *drho, double *sig) {
     long N = (long)nx * ny;
     for (int i = 0; i < 9; ++i)
-        for (long k = 0; k < N; ++k) nstar[i * N + k] = ORC_W[i] * rho[k];
+        for (long k = 0; k < N; ++k) dn[i * N + k] = ORC_W[i] * (rho[k] - 1.0);
     for (long k = 0; k < N; ++k) drho[k] = 0.0;
     if (sig)
         for (long k = 0; k < 3 * N; ++k) sig[k] = 0.0;
@@ -285,13 +304,13 @@ void orc_init(int nx, int ny, const double *rho, double *nstar, double *drho, do
 
 /* Per-node results of one update (everything the collision and the field output need). */
 typedef struct {
-    double R0, j[2];       /* zeroth moment after streaming, current j (Eq. rhoj)     */
+    double R0m1, j[2];     /* zeroth moment after streaming minus 1, current j (Eq. rhoj) */
     double kap[4];         /* kappa (xx, xy, yx, yy)                                  */
     double tau_M;          /* Eq. (nlmaxwell)                                          */
     double sigma[3];       /* polymer stress (xx, xy, yy)                             */
     double sbar[3];        /* traceless part of Sigma^nN (xx, xy, yy)                 */
     double drho, S;        /* delta rho(t) and S = delta rho(t) - delta rho(t-1)       */
-    double rho_eq, u[2];   /* density and velocity handed to n^eq                     */
+    double rho_eq_m1, u[2];/* density (minus 1) and velocity handed to n^eq           */
 } node_result;
 
 static inline long idx(int nx, int x, int y) { return (long)y * nx + x; }
@@ -315,10 +334,10 @@ static double ddx(const double *v, int nx, int x, int y, int comp) {
 /* Steps 3-6 of the header, and the density / velocity of step 7, for node (x,y): needs the
  * moments R0 / j and gradient velocity ug of every node, drho_prev and the carried stress. */
 static void node_update(const orc_params *p, int nx, int ny, int x, int y,
-                        const double *R0, const double *j, const double *ug,
+                        const double *R0m1, const double *j, const double *ug,
                         const double *drho_prev, const double *sig_prev, node_result *r) {
     long N = (long)nx * ny, k = idx(nx, x, y);
-    r->R0 = R0[k];
+    r->R0m1 = R0m1[k];
     r->j[0] = j[2 * k];
     r->j[1] = j[2 * k + 1];
     /* kappa_ab = d_b u_a */
@@ -363,14 +382,16 @@ static void node_update(const orc_params *p, int nx, int ny, int x, int y,
     r->sbar[2] = nn_yy - trace / ORC_DIM;
     r->drho = -trace / (ORC_CS2 * ORC_DIM);   /* flow-induced density change (Sec. II A) */
     r->S = r->drho - drho_prev[k];            /* dt d_t delta rho, Eq. (rhoplus)         */
-    r->rho_eq = r->R0 + 0.5 * r->S;           /* reading C1: sum_i n^eq = sum_i (n*+n)/2 */
-    r->u[0] = r->j[0] / r->rho_eq;
-    r->u[1] = r->j[1] / r->rho_eq;
+    /* reading: sum_i n^eq = sum_i (n* + n)/2 = R0 + S/2, so that sum_i (Delta_i + F_i) = S */
+    r->rho_eq_m1 = r->R0m1 + 0.5 * r->S;
+    r->u[0] = r->j[0] / (1.0 + r->rho_eq_m1);
+    r->u[1] = r->j[1] / (1.0 + r->rho_eq_m1);
 }
 
-/* Streaming (pull form of Eq. lbupdate) plus bounce-back, then the moments of Eq. (rhoj). */
-static void stream_and_moments(const orc_params *p, int nx, int ny, const double *nstar, double *n,
-                               double *R0, double *j, double *ug) {
+/* Streaming (pull form of Eq. lbupdate) plus bounce-back, then the moments of Eq. (rhoj).
+ * Works on offsets: R0 - 1 = sum_i dn_i and sum_i c_i n_i = sum_i c_i dn_i. */
+static void stream_and_moments(const orc_params *p, int nx, int ny, const double *dnstar, double *dn,
+                               double *R0m1, double *j, double *ug) {
     long N = (long)nx * ny;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
@@ -389,41 +410,41 @@ static void stream_and_moments(const orc_params *p, int nx, int ny, const double
                     int opp = -1;
                     for (int o = 0; o < 9; ++o)
                         if (ORC_CX[o] == -ORC_CX[i] && ORC_CY[o] == -ORC_CY[i]) opp = o;
-                    v = nstar[opp * N + k];
+                    v = dnstar[opp * N + k];
                 } else {
-                    v = nstar[i * N + idx(nx, xs, ys)];
+                    v = dnstar[i * N + idx(nx, xs, ys)];
                 }
-                n[i * N + k] = v;
+                dn[i * N + k] = v;
                 r0 += v;
                 jx += ORC_CX[i] * v;
                 jy += ORC_CY[i] * v;
             }
-            R0[k] = r0;
+            R0m1[k] = r0;
             j[2 * k] = jx + 0.5 * p->g_x; /* j = sum c n + f dt/2 (Eq. rhoj, with the forcing) */
             j[2 * k + 1] = jy;
-            ug[2 * k] = j[2 * k] / r0;    /* reading C2: gradients from j / R0 */
-            ug[2 * k + 1] = j[2 * k + 1] / r0;
+            ug[2 * k] = j[2 * k] / (1.0 + r0);    /* reading: gradients from j / R0 */
+            ug[2 * k + 1] = j[2 * k + 1] / (1.0 + r0);
         }
 }
 
 typedef struct {
-    double *n, *R0, *j, *ug;
+    double *n, *R0m1, *j, *ug;
 } orc_work;
 
 static int work_alloc(orc_work *w, long N) {
     w->n = (double *)malloc(sizeof(double) * 9 * N);
-    w->R0 = (double *)malloc(sizeof(double) * N);
+    w->R0m1 = (double *)malloc(sizeof(double) * N);
     w->j = (double *)malloc(sizeof(double) * 2 * N);
     w->ug = (double *)malloc(sizeof(double) * 2 * N);
-    return (w->n && w->R0 && w->j && w->ug) ? 0 : -1;
+    return (w->n && w->R0m1 && w->j && w->ug) ? 0 : -1;
 }
-static void work_free(orc_work *w) { free(w->n); free(w->R0); free(w->j); free(w->ug); }
+static void work_free(orc_work *w) { free(w->n); free(w->R0m1); free(w->j); free(w->ug); }
 
 static int valid_grid(int nx, int ny) { return nx >= 1 && ny >= 3; }
 
-/* Advance the state (nstar, drho, sig) by nsteps steps in place.  Returns 0, or -1 on a bad
+/* Advance the state (dn_star, drho, sig) by nsteps steps in place.  Returns 0, or -1 on a bad
  * argument / allocation failure. */
-int orc_run(const orc_params *p, int nx, int ny, double *nstar, double *drho, double *sig,
+int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, double *sig,
             long nsteps, int nthreads) {
     if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig)) return -1;
 #ifdef _OPENMP
@@ -435,7 +456,7 @@ int orc_run(const orc_params *p, int nx, int ny, double *nstar, double *drho, do
     orc_work w;
     if (work_alloc(&w, N)) { work_free(&w); return -1; }
     for (long s = 0; s < nsteps; ++s) {
-        stream_and_moments(p, nx, ny, nstar, w.n, w.R0, w.j, w.ug);
+        stream_and_moments(p, nx, ny, dn_star, w.n, w.R0m1, w.j, w.ug);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
 #endif
@@ -443,14 +464,15 @@ int orc_run(const orc_params *p, int nx, int ny, double *nstar, double *drho, do
             for (int x = 0; x < nx; ++x) {
                 long k = idx(nx, x, y);
                 node_result r;
-                node_update(p, nx, ny, x, y, w.R0, w.j, w.ug, drho, sig, &r);
-                double neq[9], F[9];
-                orc_equilibrium(r.rho_eq, r.u[0], r.u[1], neq);
+                node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
+                double dneq[9], F[9];
+                orc_equilibrium_offset(r.rho_eq_m1, r.u[0], r.u[1], dneq);
                 double f[2] = {p->g_x, 0.0};
                 orc_forcing(p->tau_lb, r.sbar, r.S, r.u, f, F);
                 for (int i = 0; i < 9; ++i) {
-                    double ni = w.n[i * N + k];
-                    nstar[i * N + k] = ni - (ni - neq[i]) / p->tau_lb + F[i];
+                    /* BGK: n* = n - (n - n^eq)/tau_LB + F, on offsets from w_i */
+                    double dni = w.n[i * N + k];
+                    dn_star[i * N + k] = dni - (dni - dneq[i]) / p->tau_lb + F[i];
                 }
                 drho[k] = r.drho;
                 if (p->stress_mode == 1) {
@@ -469,19 +491,19 @@ int orc_run(const orc_params *p, int nx, int ny, double *nstar, double *drho, do
  *   sigma[y][x][4] = polymer stress (xx, yy, zz, xy), zz = 0 in 2-D flow,
  *   rho[y][x]    = hydrodynamic density rho_eq - delta rho(t)  (Eq. rhoj, reading C1).
  * The state is not modified. */
-int orc_fields(const orc_params *p, int nx, int ny, const double *nstar, const double *drho,
+int orc_fields(const orc_params *p, int nx, int ny, const double *dn_star, const double *drho,
                const double *sig, double *u, double *sigma, double *rho) {
     if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig)) return -1;
     long N = (long)nx * ny;
     orc_work w;
     if (work_alloc(&w, N)) { work_free(&w); return -1; }
-    stream_and_moments(p, nx, ny, nstar, w.n, w.R0, w.j, w.ug);
+    stream_and_moments(p, nx, ny, dn_star, w.n, w.R0m1, w.j, w.ug);
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(nx, x, y);
             node_result r;
-            node_update(p, nx, ny, x, y, w.R0, w.j, w.ug, drho, sig, &r);
-            double rho_h = r.rho_eq - r.drho;
+            node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
+            double rho_h = 1.0 + (r.rho_eq_m1 - r.drho);
             if (u) { u[2 * k] = r.j[0] / rho_h; u[2 * k + 1] = r.j[1] / rho_h; }
             if (sigma) {
                 sigma[4 * k + 0] = r.sigma[0];
@@ -497,21 +519,21 @@ int orc_fields(const orc_params *p, int nx, int ny, const double *nstar, const d
 
 /* Diagnostic access to the per-node intermediates of one update (kappa, tau_M, drho, S),
  * used by tests: out[y][x][8] = kxx, kxy, kyx, kyy, tau_M, drho, S, rho_eq. */
-int orc_node_intermediates(const orc_params *p, int nx, int ny, const double *nstar,
+int orc_node_intermediates(const orc_params *p, int nx, int ny, const double *dn_star,
                            const double *drho, const double *sig, double *out) {
     if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig)) return -1;
     long N = (long)nx * ny;
     orc_work w;
     if (work_alloc(&w, N)) { work_free(&w); return -1; }
-    stream_and_moments(p, nx, ny, nstar, w.n, w.R0, w.j, w.ug);
+    stream_and_moments(p, nx, ny, dn_star, w.n, w.R0m1, w.j, w.ug);
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(nx, x, y);
             node_result r;
-            node_update(p, nx, ny, x, y, w.R0, w.j, w.ug, drho, sig, &r);
+            node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
             double *o = out + 8 * k;
             o[0] = r.kap[0]; o[1] = r.kap[1]; o[2] = r.kap[2]; o[3] = r.kap[3];
-            o[4] = r.tau_M; o[5] = r.drho; o[6] = r.S; o[7] = r.rho_eq;
+            o[4] = r.tau_M; o[5] = r.drho; o[6] = r.S; o[7] = 1.0 + r.rho_eq_m1;
         }
     work_free(&w);
     return 0;

@@ -17,6 +17,7 @@
 #include <new>
 #include <vector>
 
+#include "lb_step_march.cuh"
 #include "lb_step_tile.cuh"
 #include "lbnlm.h"
 
@@ -27,6 +28,18 @@ extern template cudaError_t launch_step_tile<float, float, 0>(const StepArgs<flo
 extern template cudaError_t launch_step_tile<float, float, 1>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<__nv_bfloat16, float, 0>(const StepArgs<__nv_bfloat16, float>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<__nv_bfloat16, float, 1>(const StepArgs<__nv_bfloat16, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<double, float, 0>(const StepArgs<double, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<double, float, 1>(const StepArgs<double, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<float, double, 0>(const StepArgs<float, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<float, double, 1>(const StepArgs<float, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_march<float, float, 0>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<float, float, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<__nv_bfloat16, float, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t march_occupancy<float, float, 0>(int*);
+extern template cudaError_t march_occupancy<float, float, 1>(int*);
+extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0>(int*);
+extern template cudaError_t march_occupancy<__nv_bfloat16, float, 1>(int*);
 }  // namespace lbk
 
 using namespace lbk;
@@ -153,10 +166,11 @@ __global__ void k_set_fields(T* pop, C* drho, C* sig3, const double* u, const do
     }
 }
 
+// Apply the per-channel body forces staged in gx (device, copied from pinned host memory).
 template <typename C>
-__global__ void k_set_gx(ChanParams<C>* chan, int n_ch, int ch, double gx) {
+__global__ void k_apply_gx(ChanParams<C>* chan, const double* gx, int n_ch) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n_ch && (ch < 0 || c == ch)) chan[c].gx = (C)gx;
+    if (c < n_ch) chan[c].gx = (C)gx[c];
 }
 
 // Per-channel reduction of the step's block partials, in a fixed order (deterministic).
@@ -203,6 +217,22 @@ int grid_for(long long n) {
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
 }
 
+// Storage type T and arithmetic type C of a precision mode.
+template <typename X> struct Tag { using type = X; };
+template <typename F>
+auto with_types(int prec, F&& f) {
+    switch (prec) {
+        case LB_PREC_F64: return f(Tag<double>{}, Tag<double>{});
+        case LB_PREC_F32: return f(Tag<float>{}, Tag<float>{});
+        case LB_PREC_BF16: return f(Tag<__nv_bfloat16>{}, Tag<float>{});
+        case LB_PREC_F64S_F32M: return f(Tag<double>{}, Tag<float>{});
+        default: return f(Tag<float>{}, Tag<double>{});
+    }
+}
+#define LB_TYPES(tt, tc)                          \
+    using T = typename decltype(tt)::type;        \
+    using C = typename decltype(tc)::type;
+
 }  // namespace
 
 struct lb_handle {
@@ -239,9 +269,21 @@ struct lb_handle {
     long uprev_state = -10;    // state index whose velocity u_prev holds
     long mon_state = -1;       // state index of the last residual evaluation (-1: none)
     int* status_h = nullptr;   // pinned
+    double* gx_h = nullptr;    // pinned staging of the body forces (h2d each lb_set_body_force)
+    cudaEvent_t gx_ev = nullptr;
+    bool gx_pending = false;
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
     bool any_unstable = false;
+    bool any_timeout = false;
+    // row-march kernel (wide single channels, FP32 / BF16 storage)
+    bool march = false;
+    CUtensorMap mapA, mapB;    // tensor maps of the two population buffers ...
+    const void* mapA_buf = nullptr;  // ... and the buffers they describe (the pointers swap)
+    const void* mapB_buf = nullptr;
+    MarchItem* march_items_d = nullptr;
+    int* march_item_begin_d = nullptr;  // {0, n_march_items}: the residual reduction's item range
+    int n_march_items = 0, march_grid = 0;
 };
 
 namespace {
@@ -306,10 +348,96 @@ void plan_tiles(lb_handle* h) {
     h->smem = (size_t)maxEX * maxEY * 2 * h->csize;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    }
+    return fn;
+}
+
+// 3-D map over the 9 population planes of channel 0: dims (nx, ny, 9), box (W + 2 HP, 1, 9).
+bool make_pop_map(const lb_handle* h, void* base, CUtensorMap* map) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const bool bf = h->prec == LB_PREC_BF16;
+    const cuuint64_t es = bf ? 2 : 4;
+    const cuuint32_t hp = (cuuint32_t)(16 / es);
+    cuuint64_t dims[3] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny[0], 9};
+    cuuint64_t strides[2] = {(cuuint64_t)h->nx * es, (cuuint64_t)h->P[0] * es};
+    cuuint32_t box[3] = {(cuuint32_t)kMarchW + 2 * hp, 1, 9};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Row-march plan: strips of kMarchW columns; the rows split into balanced chunks so that the
+// work items fill one wave of resident CTAs.
+lb_status plan_march(lb_handle* h) {
+    h->march = false;
+    if (h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
+        h->ny[0] < 16 || (h->flags & LB_GRID_TILE_ONLY))
+        return LB_OK;
+    if (!make_pop_map(h, h->popA, &h->mapA) || !make_pop_map(h, h->popB, &h->mapB)) return LB_OK;
+    h->mapA_buf = h->popA;
+    h->mapB_buf = h->popB;
+    int bps = 0, nsm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
+    if (e == cudaSuccess) {
+        if (h->prec == LB_PREC_F32) e = h->smode ? march_occupancy<float, float, 1>(&bps) : march_occupancy<float, float, 0>(&bps);
+        else e = h->smode ? march_occupancy<__nv_bfloat16, float, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0>(&bps);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "lb_create: march occupancy");
+    if (bps < 1) return LB_OK;
+    const int strips = h->nx / kMarchW;
+    const int slots = bps * nsm;
+    // one wave: at most as many items as resident CTAs (a partial second wave would double the
+    // kernel time for a few CTAs)
+    int chunks = slots / strips;
+    if (chunks > h->ny[0] / 8) chunks = h->ny[0] / 8;
+    if (chunks < 1) chunks = 1;
+    std::vector<MarchItem> items;
+    for (int c = 0; c < chunks; ++c)
+        for (int s = 0; s < strips; ++s) {
+            MarchItem it{};
+            it.x0 = s * kMarchW;
+            it.y0 = (int)((long long)h->ny[0] * c / chunks);
+            it.y1 = (int)((long long)h->ny[0] * (c + 1) / chunks);
+            items.push_back(it);
+        }
+    LB_CK(cudaMalloc(&h->march_items_d, sizeof(MarchItem) * items.size()));
+    LB_CK(cudaMemcpy(h->march_items_d, items.data(), sizeof(MarchItem) * items.size(), cudaMemcpyHostToDevice));
+    h->n_march_items = (int)items.size();
+    const int ib[2] = {0, h->n_march_items};
+    LB_CK(cudaMalloc(&h->march_item_begin_d, sizeof(ib)));
+    LB_CK(cudaMemcpy(h->march_item_begin_d, ib, sizeof(ib), cudaMemcpyHostToDevice));
+    if ((int)h->items.size() < h->n_march_items) {  // the partials buffer serves both plans
+        cudaFree(h->partials);
+        h->partials = nullptr;
+        LB_CK(cudaMalloc(&h->partials, 4 * sizeof(double) * h->n_march_items));
+    }
+    h->march_grid = std::min(h->n_march_items, slots);
+    h->march = true;
+    return LB_OK;
+}
+
 lb_status validate(const lb_grid* g, const lb_params* p, const lb_boundary* b) {
     if (!g || !p || !b) return fail(LB_EINVAL, "lb_create: null argument%s");
     if (g->n_channels < 1 || g->nx < 1 || !g->ny) return fail(LB_EINVAL, "lb_create: need n_channels >= 1, nx >= 1, ny%s");
-    if (g->precision < 0 || g->precision > 2) return fail(LB_EINVAL, "lb_create: unknown precision%s");
+    if (g->precision < 0 || g->precision > 4) return fail(LB_EINVAL, "lb_create: unknown precision%s");
     if (g->stress_mode < 0 || g->stress_mode > 1) return fail(LB_EINVAL, "lb_create: unknown stress_mode%s");
     if (b->walls != 1 || b->periodic_x != 1)
         return fail(LB_EINVAL, "lb_create: only bounce-back walls with periodic x are supported%s");
@@ -343,8 +471,12 @@ void release(lb_handle* h) {
     free_dev(h->partials); free_dev(h->mon_d); free_dev(h->status_d); free_dev(h->base_d); free_dev(h->P_d);
     free_dev(h->node_off_d); free_dev(h->ny_d); free_dev(h->gx_d); free_dev(h->fields); free_dev(h->fconv);
     free_dev(h->hstage);
+    free_dev(h->march_items_d);
+    free_dev(h->march_item_begin_d);
     if (h->status_h) cudaFreeHost(h->status_h);
+    if (h->gx_h) cudaFreeHost(h->gx_h);
     if (h->status_ev) cudaEventDestroy(h->status_ev);
+    if (h->gx_ev) cudaEventDestroy(h->gx_ev);
     delete h;
 }
 
@@ -382,6 +514,24 @@ cudaError_t launch(lb_handle* h, const StepArgs<T, C>& a) {
     return launch_step_tile<T, C, 1>(a, n, h->smem, h->stream);
 }
 
+// The row-march kernel takes plain steps (no fields output, no residual reduction).
+template <typename T, typename C>
+cudaError_t launch_march(lb_handle*, const StepArgs<T, C>&) { return cudaErrorNotSupported; }
+template <>
+cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float>& a) {
+    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d};
+    const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
+    return h->smode ? launch_step_march<float, float, 1>(m, a, ctl, h->march_grid, h->stream)
+                    : launch_step_march<float, float, 0>(m, a, ctl, h->march_grid, h->stream);
+}
+template <>
+cudaError_t launch_march<__nv_bfloat16, float>(lb_handle* h, const StepArgs<__nv_bfloat16, float>& a) {
+    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d};
+    const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
+    return h->smode ? launch_step_march<__nv_bfloat16, float, 1>(m, a, ctl, h->march_grid, h->stream)
+                    : launch_step_march<__nv_bfloat16, float, 0>(m, a, ctl, h->march_grid, h->stream);
+}
+
 template <typename T, typename C>
 lb_status run_steps(lb_handle* h, long n) {
     for (long s = 1; s <= n; ++s) {
@@ -392,10 +542,11 @@ lb_status run_steps(lb_handle* h, long n) {
         if (s >= n - 1) f |= F_SAVE_U;
         if (resid) f |= F_RESID;
         a.flags = f;
-        LB_CK((launch<T, C>(h, a)));
+        if (h->march) LB_CK((launch_march<T, C>(h, a)));
+        else LB_CK((launch<T, C>(h, a)));
         if (resid) {
-            k_reduce_residual<<<h->n_ch, kThreads, 0, h->stream>>>(h->partials, h->item_begin_d, h->status_d,
-                                                                    h->mon_d, h->nx, h->step);
+            k_reduce_residual<<<h->n_ch, kThreads, 0, h->stream>>>(h->partials, h->march ? h->march_item_begin_d : h->item_begin_d,
+                                                                    h->status_d, h->mon_d, h->nx, h->step);
             LB_CK(cudaGetLastError());
             h->mon_state = h->step;
         }
@@ -422,8 +573,10 @@ lb_status poll_status(lb_handle* h, bool wait) {
         cudaError_t q = wait ? cudaEventSynchronize(h->status_ev) : cudaEventQuery(h->status_ev);
         if (q == cudaSuccess) {
             h->status_pending = false;
-            for (int c = 0; c < h->n_ch; ++c)
-                if (h->status_h[c]) h->any_unstable = true;
+            for (int c = 0; c < h->n_ch; ++c) {
+                if (h->status_h[c] & 1) h->any_unstable = true;
+                if (h->status_h[c] & 2) h->any_timeout = true;
+            }
         } else if (q != cudaErrorNotReady) {
             return cuda_fail(q, "status event");
         }
@@ -473,8 +626,8 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     h->prec = grid->precision;
     h->smode = grid->stress_mode;
     h->flags = grid->flags;
-    h->tsize = h->prec == LB_PREC_F64 ? 8 : (h->prec == LB_PREC_F32 ? 4 : 2);
-    h->csize = h->prec == LB_PREC_F64 ? 8 : 4;
+    h->tsize = with_types(h->prec, [](auto tt, auto tc) { LB_TYPES(tt, tc); (void)sizeof(C); return sizeof(T); });
+    h->csize = with_types(h->prec, [](auto tt, auto tc) { LB_TYPES(tt, tc); (void)sizeof(T); return sizeof(C); });
     h->ny.assign(grid->ny, grid->ny + h->n_ch);
     h->params.assign(params, params + h->n_ch);
     h->P.resize(h->n_ch); h->base.resize(h->n_ch); h->node_off.resize(h->n_ch);
@@ -518,7 +671,10 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
 #undef LB_ALLOC
     e = cudaMallocHost((void**)&h->status_h, h->n_ch * sizeof(int));
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
+    e = cudaMallocHost((void**)&h->gx_h, h->n_ch * sizeof(double));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
     e = cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gx_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaEventCreate"));
 
     // tables (synchronous copies: creation is not on the hot path)
@@ -555,15 +711,17 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     long long maxn = 0;
     for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
     dim3 g(grid_for(maxn), h->n_ch);
-    switch (h->prec) {
-        case LB_PREC_F64: k_init<double, double><<<g, 256, 0, h->stream>>>((double*)h->popA, (double*)h->drho, (double*)h->sig3, ic_d, h->nx, h->smode); break;
-        case LB_PREC_F32: k_init<float, float><<<g, 256, 0, h->stream>>>((float*)h->popA, (float*)h->drho, (float*)h->sig3, ic_d, h->nx, h->smode); break;
-        default: k_init<__nv_bfloat16, float><<<g, 256, 0, h->stream>>>((__nv_bfloat16*)h->popA, (float*)h->drho, (float*)h->sig3, ic_d, h->nx, h->smode); break;
-    }
+    with_types(h->prec, [&](auto tt, auto tc) {
+        LB_TYPES(tt, tc);
+        k_init<T, C><<<g, 256, 0, h->stream>>>((T*)h->popA, (C*)h->drho, (C*)h->sig3, ic_d, h->nx, h->smode);
+        return 0;
+    });
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(ic_d);
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: init kernel"));
+    st = plan_march(h);
+    if (st != LB_OK) return bail(st);
     *out = h;
     return LB_OK;
 }
@@ -571,18 +729,16 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
 void lb_destroy(lb_handle* h) { release(h); }
 
 long lb_step_count(const lb_handle* h) { return h ? h->step : -1; }
+int lb_uses_row_march(const lb_handle* h) { return (h && h->march) ? 1 : 0; }
 size_t lb_num_nodes(const lb_handle* h) { return h ? (size_t)h->nodes : 0; }
 
 lb_status lb_step(lb_handle* h, long n) {
     if (!h || n < 0) return fail(LB_EINVAL, "lb_step: bad handle or n%s");
     lb_status st = poll_status(h, false);
     if (st != LB_OK) return st;
+    if (h->any_timeout) return fail(LB_ETIMEOUT, "lb_step: a device-side wait timed out earlier%s");
     if (n == 0) return h->any_unstable ? LB_EUNSTABLE : LB_OK;
-    switch (h->prec) {
-        case LB_PREC_F64: st = run_steps<double, double>(h, n); break;
-        case LB_PREC_F32: st = run_steps<float, float>(h, n); break;
-        default: st = run_steps<__nv_bfloat16, float>(h, n); break;
-    }
+    st = with_types(h->prec, [&](auto tt, auto tc) { LB_TYPES(tt, tc); return run_steps<T, C>(h, n); });
     if (st != LB_OK) return st;
     if (!h->status_pending) {
         st = request_status(h);
@@ -601,11 +757,7 @@ lb_status lb_get_fields(lb_handle* h, void* u, void* sigma, void* rho, int out_d
     void* fs = base + 2 * N * h->csize;
     void* fr = base + 6 * N * h->csize;
     lb_status st;
-    switch (h->prec) {
-        case LB_PREC_F64: st = fields_pass<double, double>(h, (double*)fu, (double*)fs, (double*)fr); break;
-        case LB_PREC_F32: st = fields_pass<float, float>(h, (float*)fu, (float*)fs, (float*)fr); break;
-        default: st = fields_pass<__nv_bfloat16, float>(h, (float*)fu, (float*)fs, (float*)fr); break;
-    }
+    st = with_types(h->prec, [&](auto tt, auto tc) { LB_TYPES(tt, tc); return fields_pass<T, C>(h, (C*)fu, (C*)fs, (C*)fr); });
     if (st != LB_OK) return st;
     const size_t osize = out_dtype == 0 ? 8 : 4;
     const void* src = h->fields;
@@ -647,13 +799,15 @@ lb_status lb_set_body_force(lb_handle* h, int channel, double g_x) {
         return fail(LB_EINVAL, "lb_set_body_force: bad argument%s");
     for (int c = 0; c < h->n_ch; ++c)
         if (channel < 0 || c == channel) h->params[c].g_x = g_x;
-    if (h->csize == 8) k_set_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->n_ch, channel, g_x);
-    else k_set_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->n_ch, channel, g_x);
+    // stream-ordered: the pinned staging buffer is reused only after its previous copy ran
+    if (h->gx_pending) LB_CK(cudaEventSynchronize(h->gx_ev));
+    for (int c = 0; c < h->n_ch; ++c) h->gx_h[c] = h->params[c].g_x;
+    LB_CK(cudaMemcpyAsync(h->gx_d, h->gx_h, sizeof(double) * h->n_ch, cudaMemcpyHostToDevice, h->stream));
+    LB_CK(cudaEventRecord(h->gx_ev, h->stream));
+    h->gx_pending = true;
+    if (h->csize == 8) k_apply_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->gx_d, h->n_ch);
+    else k_apply_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->gx_d, h->n_ch);
     LB_CK(cudaGetLastError());
-    std::vector<double> gx(h->n_ch);
-    for (int c = 0; c < h->n_ch; ++c) gx[c] = h->params[c].g_x;
-    LB_CK(cudaStreamSynchronize(h->stream));
-    LB_CK(cudaMemcpy(h->gx_d, gx.data(), sizeof(double) * h->n_ch, cudaMemcpyHostToDevice));
     return LB_OK;
 }
 
@@ -671,11 +825,12 @@ lb_status lb_set_fields(lb_handle* h, const double* u, const double* rho, const 
     long long maxn = 0;
     for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
     dim3 g(grid_for(maxn), h->n_ch);
-    switch (h->prec) {
-        case LB_PREC_F64: k_set_fields<double, double><<<g, 256, 0, h->stream>>>((double*)h->popA, (double*)h->drho, (double*)h->sig3, su, sr, drho ? sd : nullptr, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode); break;
-        case LB_PREC_F32: k_set_fields<float, float><<<g, 256, 0, h->stream>>>((float*)h->popA, (float*)h->drho, (float*)h->sig3, su, sr, drho ? sd : nullptr, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode); break;
-        default: k_set_fields<__nv_bfloat16, float><<<g, 256, 0, h->stream>>>((__nv_bfloat16*)h->popA, (float*)h->drho, (float*)h->sig3, su, sr, drho ? sd : nullptr, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode); break;
-    }
+    with_types(h->prec, [&](auto tt, auto tc) {
+        LB_TYPES(tt, tc);
+        k_set_fields<T, C><<<g, 256, 0, h->stream>>>((T*)h->popA, (C*)h->drho, (C*)h->sig3, su, sr, drho ? sd : nullptr,
+                                                     h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode);
+        return 0;
+    });
     LB_CK(cudaGetLastError());
     LB_CK(cudaStreamSynchronize(h->stream));
     h->uprev_state = -10;
@@ -692,11 +847,11 @@ lb_status lb_set_populations(lb_handle* h, const double* n, const double* drho, 
     dim3 g(grid_for(maxn), h->n_ch);
     double* s = (double*)h->hstage;
     LB_CK(cudaMemcpyAsync(s, n, 9 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    switch (h->prec) {
-        case LB_PREC_F64: k_pop_from_f64<double, double><<<g, 256, 0, h->stream>>>((double*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
-        case LB_PREC_F32: k_pop_from_f64<float, float><<<g, 256, 0, h->stream>>>((float*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
-        default: k_pop_from_f64<__nv_bfloat16, float><<<g, 256, 0, h->stream>>>((__nv_bfloat16*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
-    }
+    with_types(h->prec, [&](auto tt, auto tc) {
+        LB_TYPES(tt, tc);
+        k_pop_from_f64<T, C><<<g, 256, 0, h->stream>>>((T*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+        return 0;
+    });
     LB_CK(cudaGetLastError());
     LB_CK(cudaMemcpyAsync(s, drho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (h->csize == 8) k_planes_from_f64<double><<<g, 256, 0, h->stream>>>((double*)h->drho, s, 1, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
@@ -727,11 +882,11 @@ lb_status lb_get_populations(lb_handle* h, double* n, double* drho, double* sig3
     for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
     dim3 g(grid_for(maxn), h->n_ch);
     double* s = (double*)h->hstage;
-    switch (h->prec) {
-        case LB_PREC_F64: k_pop_to_f64<double, double><<<g, 256, 0, h->stream>>>((const double*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
-        case LB_PREC_F32: k_pop_to_f64<float, float><<<g, 256, 0, h->stream>>>((const float*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
-        default: k_pop_to_f64<__nv_bfloat16, float><<<g, 256, 0, h->stream>>>((const __nv_bfloat16*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx); break;
-    }
+    with_types(h->prec, [&](auto tt, auto tc) {
+        LB_TYPES(tt, tc);
+        k_pop_to_f64<T, C><<<g, 256, 0, h->stream>>>((const T*)h->popA, s, h->base_d, h->P_d, h->node_off_d, h->ny_d, h->nx);
+        return 0;
+    });
     LB_CK(cudaGetLastError());
     LB_CK(cudaMemcpyAsync(n, s, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
@@ -805,8 +960,10 @@ lb_status lb_channel_status(lb_handle* h, int* status) {
     if (!h || !status) return fail(LB_EINVAL, "lb_channel_status: null argument%s");
     LB_CK(cudaMemcpyAsync(status, h->status_d, sizeof(int) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
-    for (int c = 0; c < h->n_ch; ++c)
-        if (status[c]) h->any_unstable = true;
+    for (int c = 0; c < h->n_ch; ++c) {
+        if (status[c] & 1) h->any_unstable = true;
+        if (status[c] & 2) h->any_timeout = true;
+    }
     return LB_OK;
 }
 

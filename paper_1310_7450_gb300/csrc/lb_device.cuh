@@ -33,16 +33,19 @@ __host__ __device__ constexpr C wgt(int i) {
 template <typename T> struct Store;
 template <> struct Store<double> {
     using C = double;
+    static __device__ __forceinline__ double cvt(double v) { return v; }
     static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
 template <> struct Store<float> {
     using C = float;
+    static __device__ __forceinline__ float cvt(float v) { return v; }
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <> struct Store<__nv_bfloat16> {
     using C = float;
+    static __device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
@@ -104,6 +107,19 @@ struct StepArgs {
 
 // ---- per-node arithmetic -------------------------------------------------------------------
 
+// Division and square root: exact IEEE operations in FP64 (the parity mode); in FP32 CUDA's fast
+// intrinsics (__fdividef and rsqrtf, 2 ulp) -- every denominator here is a density near 1 or a
+// positive quantity in the normal range, and the FP32 path's parity bound is 1e-5.
+template <typename C> struct Arith;
+template <> struct Arith<double> {
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+};
+template <> struct Arith<float> {
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+};
+
 // Moments of Eq. (rhoj) from the post-streaming deviations: dR = sum_i n_i - 1, J0 = sum c_i n_i.
 template <typename C>
 __device__ __forceinline__ void moments(const C (&d)[9], C& dR, C& jx, C& jy) {
@@ -114,12 +130,12 @@ __device__ __forceinline__ void moments(const C (&d)[9], C& dR, C& jx, C& jy) {
 
 // Velocity used for the gradients (reading: j / R0 with R0 = sum_i n_i after streaming, because
 // the density of Eq. (rhoj) needs S, which needs sigma(kappa)); one routine for the own node and
-// the halo ring so that both give bit-identical values.
+// the halo nodes so that both give bit-identical values.
 template <typename C>
 __device__ __forceinline__ void gradient_velocity(const C (&d)[9], C gx, C& dR, C& jx, C& jy, C& ux, C& uy) {
     moments<C>(d, dR, jx, jy);
     jx = jx + C(0.5) * gx;  // j = sum c n + f dt/2 (Eq. rhoj)
-    const C inv = C(1) / (C(1) + dR);
+    const C inv = Arith<C>::div(C(1), C(1) + dR);
     ux = jx * inv;
     uy = jy * inv;
 }
@@ -137,15 +153,11 @@ __device__ __forceinline__ void convected_solve(C ka, C kb, C kc, C ke, C alpha,
     const C E = C(1) - C(2) * alpha * ke;
     const C Pp = C(1) - alpha * (ka + ke);
     const C q = alpha * alpha * kb * kc;
-    const C inv_det = C(1) / (Pp * (A * E - C(4) * q));
+    const C inv_det = Arith<C>::div(C(1), Pp * (A * E - C(4) * q));
     sxy = (alpha * kc * E * b1 + A * E * b2 + alpha * kb * A * b3) * inv_det;
     sxx = ((Pp * E - C(2) * q) * b1 + C(2) * alpha * kb * E * b2 + C(2) * alpha * alpha * kb * kb * b3) * inv_det;
     syy = (C(2) * alpha * alpha * kc * kc * b1 + C(2) * alpha * kc * A * b2 + (A * Pp - C(2) * q) * b3) * inv_det;
 }
-
-template <typename C> __device__ __forceinline__ C csqrt(C v);
-template <> __device__ __forceinline__ double csqrt<double>(double v) { return sqrt(v); }
-template <> __device__ __forceinline__ float csqrt<float>(float v) { return sqrtf(v); }
 
 // Everything between the moments and the collision for one node (Sec. II A and III A):
 // kappa -> tau_M (Eq. nlmaxwell) -> sigma -> Sigma^nN -> delta rho, S (Eq. rhoplus) ->
@@ -167,13 +179,13 @@ __device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C k
     const C Dxx = C(2) * ka, Dxy = kb + kc, Dyy = C(2) * ke;
     const C II = C(0.5) * (Dxx * Dxx + C(2) * Dxy * Dxy + Dyy * Dyy);  // (1/2) tr D^2
     C tau_M = C(0);
-    if (P.tau > C(0)) tau_M = P.tau / (C(1) + P.tau * csqrt<C>(II) * P.inv_gc);
+    if (P.tau > C(0)) tau_M = Arith<C>::div(P.tau, C(1) + P.tau * Arith<C>::sqrt(II) * P.inv_gc);
     if (tau_M > C(0)) {
         if (SMODE == 0) {
             const C gt = P.G * tau_M;
             convected_solve<C>(ka, kb, kc, ke, tau_M, gt * Dxx, gt * Dxy, gt * Dyy, r.sxx, r.sxy, r.syy);
         } else {
-            const C pre = tau_M / (tau_M + C(1));
+            const C pre = Arith<C>::div(tau_M, tau_M + C(1));
             convected_solve<C>(ka, kb, kc, ke, pre, pre * (s_old_xx + P.G * Dxx), pre * (s_old_xy + P.G * Dxy),
                                pre * (s_old_yy + P.G * Dyy), r.sxx, r.sxy, r.syy);
         }
@@ -189,25 +201,77 @@ __device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C k
     r.Bxx = C(0.5) * (Nxx - Nyy);
     r.Bxy = Nxy;
     r.dReq = dR + C(0.5) * r.S;
-    const C inv = C(1) / (C(1) + r.dReq);
+    const C inv = Arith<C>::div(C(1), C(1) + r.dReq);
     r.ux = jx * inv;
     r.uy = jy * inv;
     return r;
 }
 
-// Equilibrium (Eq. neq) minus w_i, forcing term (Eq. bodyforce) and BGK, direction i.
-template <typename C, int I>
-__device__ __forceinline__ C collide_dir(const ChanParams<C>& P, const NodeState<C>& s, C di, C usq,
-                                         C Yxx, C Yyy, C Yxy) {
-    constexpr int X = cx(I), Y = cy(I);
-    const C w = wgt<C>(I);
-    const C cu = C(X) * s.ux + C(Y) * s.uy;
-    const C neq_dev = w * (s.dReq + (C(1) + s.dReq) * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * usq));
-    // Sigma-bar : Q_i with Byy = -Bxx;  Y : Q_i with Q_i = c_i c_i - 1/3
-    const C qs = s.Bxx * C(X * X - Y * Y) + C(2 * X * Y) * s.Bxy;
-    const C qy = Yxx * (C(X * X) - C(1) / C(3)) + Yyy * (C(Y * Y) - C(1) / C(3)) + C(2 * X * Y) * Yxy;
-    const C F = w * (P.k1 * qs + P.k2 * (s.S + C(3) * C(X) * P.gx + C(4.5) * qy));
-    return di - P.omega * (di - neq_dev) + F;
+// Collision increments D_i = Delta_i + F_i = F_i + (n^eq_i - n_i)/tau_LB, with n^eq of Eq. (neq)
+// as an offset from w_i and F_i of Eq. (bodyforce).  Opposite directions share the parts that are
+// even in c_i (E) and differ in the sign of the odd part (O):
+//   E = w [ (dReq - 1.5 rq u^2)/tau + k2 S + 4.5 (rq (c.u)^2/tau + k2 Q:Y) + k1 Sbar:Q ],
+//   O = w 3 (rq (c.u)/tau + k2 c.f),     D(+c) = E + O - d/tau,  D(-c) = E - O - d/tau,
+// rq = rho_eq, Y = -S u u + u f + f u, k1 = -1/(2 c_s^4 tau_LB), k2 = 1 - 1/(2 tau_LB).
+// In exact arithmetic the increments carry mass S and momentum f (the conditions below
+// Eq. lbfab).  In FP32 the rounding of n^eq repeats identically every step of a near-steady flow
+// and would act as a spurious force (~1e-11 per step against forces of ~1e-7), so three
+// increments are closed from those conditions instead of being evaluated: direction 3 from the
+// x momentum f_x, direction 4 from the y momentum 0, and the rest direction from the mass S.
+// In exact arithmetic the closed values equal the evaluated ones.
+template <typename C>
+__device__ __forceinline__ void collide_node(const ChanParams<C>& P, const NodeState<C>& s, const C (&d)[9], C (&D)[9]) {
+    const C ux = s.ux, uy = s.uy, om = P.omega, k2 = P.k2, gx = P.gx;
+    const C rq = C(1) + s.dReq;
+    const C orq = om * rq;
+    const C usq = ux * ux + uy * uy;
+    const C Yxx = -s.S * ux * ux + C(2) * ux * gx;
+    const C Yyy = -s.S * uy * uy;
+    const C Yxy = -s.S * ux * uy + uy * gx;
+    const C trY3 = (Yxx + Yyy) * (C(1) / C(3));
+    const C base = om * (s.dReq - C(1.5) * rq * usq) + k2 * s.S;
+    const C w1 = wgt<C>(1), w5 = wgt<C>(5);
+    // (1, 3): c = +-(1, 0)
+    {
+        const C cu = ux;
+        const C E = w1 * (base + C(4.5) * (orq * cu * cu + k2 * (Yxx - trY3)) + P.k1 * s.Bxx);
+        const C O = w1 * C(3) * (orq * cu + k2 * gx);
+        D[1] = E + O - om * d[1];
+    }
+    // (2, 4): c = +-(0, 1)
+    {
+        const C cu = uy;
+        const C E = w1 * (base + C(4.5) * (orq * cu * cu + k2 * (Yyy - trY3)) - P.k1 * s.Bxx);
+        const C O = w1 * C(3) * (orq * cu);
+        D[2] = E + O - om * d[2];
+    }
+    // (5, 7): c = +-(1, 1)
+    {
+        const C cu = ux + uy;
+        const C E = w5 * (base + C(4.5) * (orq * cu * cu + k2 * (Yxx + Yyy + C(2) * Yxy - trY3)) + C(2) * P.k1 * s.Bxy);
+        const C O = w5 * C(3) * (orq * cu + k2 * gx);
+        D[5] = E + O - om * d[5];
+        D[7] = E - O - om * d[7];
+    }
+    // (8, 6): c = +-(1, -1)
+    {
+        const C cu = ux - uy;
+        const C E = w5 * (base + C(4.5) * (orq * cu * cu + k2 * (Yxx + Yyy - C(2) * Yxy - trY3)) - C(2) * P.k1 * s.Bxy);
+        const C O = w5 * C(3) * (orq * cu + k2 * gx);
+        D[8] = E + O - om * d[8];
+        D[6] = E - O - om * d[6];
+    }
+    // closures: sum c_x D = f_x, sum c_y D = 0, sum D = S
+    const C d57 = D[5] - D[7];
+    D[3] = D[1] + d57 + (D[8] - D[6]) - gx;
+    D[4] = D[2] + d57 + (D[6] - D[8]);
+    D[0] = s.S - (((D[1] + D[2]) + (D[3] + D[4])) + ((D[5] + D[6]) + (D[7] + D[8])));
+}
+
+// |u| <= guard for the reported velocity j/rho_h without a division or square root (false for NaN).
+template <typename C>
+__device__ __forceinline__ bool velocity_ok(C jx, C jy, C rho_h, C guard) {
+    return jx * jx + jy * jy <= guard * guard * rho_h * rho_h;
 }
 
 }  // namespace lbk

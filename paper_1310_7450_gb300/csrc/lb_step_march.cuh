@@ -1,0 +1,411 @@
+// lb_step_march.cuh -- the fused lattice-Boltzmann step for wide channels: a TMA-fed row march.
+//
+// A CTA of W threads owns a strip of W columns (x0 .. x0+W-1) and marches through rows y0..y1-1
+// of one channel.  The post-collision populations of the previous step stream into a ring of K
+// shared-memory slots, one source row per slot: a single 3-D tensor-memory-access copy brings the
+// 9 direction planes of that row, columns x0-HP .. x0+W+HP-1 (HP = 16 bytes of halo on each side,
+// so every copy starts on a 16-byte boundary).  The copies run K-2 rows ahead of the arithmetic
+// and complete on one mbarrier per slot.
+//
+// Per row y (one __syncthreads per row):
+//   1. moments (Eq. rhoj) of row y+1 for the W own columns and the two halo columns x0-1, x0+W,
+//      pulled from slots y, y+1, y+2 (Eq. lbupdate, pull form; bounce-back at the walls,
+//      Sec. II B); the own populations stay in registers for the next row's collision;
+//      the gradient velocity j/R0 goes into a 4-row ring in shared memory;
+//   2. barrier; one thread refills the slot of row y with row y+K;
+//   3. collision of row y: kappa by three-point differences from the velocity ring, the nlM
+//      stress, Sigma^nN, delta rho, n^eq, F_i (Eq. bodyforce), BGK; coalesced stores.
+// The periodic wrap of x is patched into the halo columns of the first and last strip with
+// plain loads.  Every mbarrier wait is bounded: on timeout the CTA records LB_ETIMEOUT in the
+// status word, drains its own copies (also bounded) and returns.
+#pragma once
+
+#include <cuda.h>
+
+#include "lb_device.cuh"
+
+namespace lbk {
+
+struct MarchItem {
+    int x0, y0, y1, pad_;
+};
+
+struct MarchCtl {
+    const MarchItem* items;
+    int n_items;
+    int* timeout_flag;  // the channel status word: bit 2 is set when a bounded wait gave up
+};
+
+// ---- PTX helpers (mbarrier, TMA) ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase with the given parity: mbarrier.try_wait suspends the thread until
+// the phase completes or a hardware time limit passes; the loop gives up after max_ns of wall
+// time (returns false then).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t max_ns) {
+    const uint32_t a = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (uint32_t k = 0;; ++k) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (k == 0) t0 = global_ns();
+        else if (global_ns() - t0 > max_ns) return false;
+    }
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+template <typename T>
+struct MarchGeom {
+    static constexpr int HP = 16 / (int)sizeof(T);  // halo columns per side (16 bytes)
+};
+
+// Shared-memory footprint of the march kernel (bytes).
+template <typename T, typename C, int W, int K>
+constexpr size_t march_smem_bytes() {
+    constexpr int HP = MarchGeom<T>::HP;
+    constexpr size_t slot = ((size_t)9 * (W + 2 * HP) * sizeof(T) + 127) / 128 * 128;
+    return 128 /*barriers*/ + K * slot + (size_t)4 * (W + 2) * 2 * sizeof(C);
+}
+
+template <typename T, typename C, int SMODE, int W, int K>
+__global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUtensorMap tmap, const StepArgs<T, C> a,
+                                                  const MarchCtl ctl) {
+    constexpr int HP = MarchGeom<T>::HP;
+    constexpr int SW = W + 2 * HP;                                   // slot row width (elements)
+    constexpr size_t SLOT = ((size_t)9 * SW * sizeof(T) + 127) / 128 * 128;
+    constexpr uint32_t TX = 9u * SW * sizeof(T);                     // bytes per copy
+    constexpr uint64_t MAXWAIT = 2000000000ull;                      // bounded waits: 2 s
+    constexpr int UW = W + 2;                                         // velocity ring row width
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);               // K mbarriers (<= 16)
+    unsigned char* slots = smem + 128;
+    C* uring = reinterpret_cast<C*>(slots + K * SLOT);                // [4][UW][2]
+
+    const int t = threadIdx.x;
+    const ChanParams<C> P = a.chan[0];
+    const int nx = a.nx, ny = P.ny;
+    if (a.status[0] != 0) return;
+
+    __shared__ int s_bad;  // set by any thread whose bounded wait gave up; read after a barrier
+    if (t == 0) {
+        s_bad = 0;
+        prefetch_tmap(&tmap);
+        for (int k = 0; k < K; ++k) mbar_init(&bars[k], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    uint32_t nload = 0;  // CTA-uniform count of copies issued (and, in order, consumed)
+    bool bad = false;
+
+    auto slot_ptr = [&](uint32_t idx) -> const T* { return reinterpret_cast<const T*>(slots + (idx % K) * SLOT); };
+    uint32_t last_issued[K];  // thread 0: index of the last copy issued into each slot
+#pragma unroll
+    for (int k = 0; k < K; ++k) last_issued[k] = 0xffffffffu;
+    auto issue = [&](uint32_t idx, int x0, int row) {  // thread 0 only
+        uint64_t* b = &bars[idx % K];
+        mbar_expect_tx(b, TX);
+        tma_load_3d(slots + (idx % K) * SLOT, &tmap, b, x0 - HP, row, 0);
+        last_issued[idx % K] = idx;
+    };
+
+    for (int item = blockIdx.x; item < ctl.n_items && !bad; item += gridDim.x) {
+        const MarchItem it = ctl.items[item];
+        const int x0 = it.x0, y0 = it.y0, y1 = it.y1;
+        const int rbase = y0 - 2;                 // first source row of this item
+        const int rlast = y1 + 1;                 // last source row
+        const uint32_t L0 = nload;                // load index of row rbase
+        const bool left_edge = (x0 == 0), right_edge = (x0 + W == nx);
+        const int x = x0 + t;
+
+        // index of the copy holding source row r, and the wait for it
+        auto idx_of = [&](int r) -> uint32_t { return L0 + (uint32_t)(r - rbase); };
+        auto wait_row = [&](int r) -> bool {
+            const uint32_t i = idx_of(r);
+            return mbar_wait(&bars[i % K], (i / K) & 1u, MAXWAIT);
+        };
+        // periodic wrap: the edge strips' halo columns x0-2, x0-1 (left) or x0+W, x0+W+1 (right)
+        // come from the other end of the row; threads 0..17 (left) and 32..49 (right) each own
+        // one (direction, column) value, loaded two rows before it is patched into its slot
+        const bool patcher = (left_edge && t < 18) || (right_edge && t >= 32 && t < 50);
+        const int pi = left_edge && t < 18 ? (t >> 1) : ((t - 32) >> 1);             // direction
+        const int pc = left_edge && t < 18 ? (nx - 2 + (t & 1)) : ((t - 32) & 1);     // global column
+        const int ps = left_edge && t < 18 ? (HP - 2 + (t & 1)) : (HP + W + ((t - 32) & 1));  // slot column
+        auto patch_load = [&](int r) -> T {
+            return (r >= 0 && r < ny && r <= rlast) ? a.pin[9 * P.base + (long long)pi * P.P + (long long)r * nx + pc] : T(0);
+        };
+        auto patch_store = [&](int r, T v) {
+            if (r >= 0 && r < ny && r <= rlast) const_cast<T*>(slot_ptr(idx_of(r)))[pi * SW + ps] = v;
+        };
+        // pulled populations of node (col, r) from the slots (col relative to x0, may be -1 or W):
+        // direction i comes from source row r - cy_i, column col - cx_i
+        auto pull = [&](int col, int r, C (&d)[9]) {
+            const T* s0 = slot_ptr(idx_of(r)) + HP + col;
+            if (r > 0 && r < ny - 1) {
+                const T* sm = slot_ptr(idx_of(r - 1)) + HP + col;  // source row r-1 (cy = +1)
+                const T* sp = slot_ptr(idx_of(r + 1)) + HP + col;  // source row r+1 (cy = -1)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const T* sr = cy(i) == 1 ? sm : (cy(i) == -1 ? sp : s0);
+                    d[i] = (C)Store<T>::cvt(sr[i * SW - cx(i)]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int rs = r - cy(i);
+                    if (rs < 0 || rs >= ny) {
+                        d[i] = (C)Store<T>::cvt(s0[opp(i) * SW]);  // bounce-back at the wall
+                    } else {
+                        const T* sr = slot_ptr(idx_of(rs)) + HP + col;
+                        d[i] = (C)Store<T>::cvt(sr[i * SW - cx(i)]);
+                    }
+                }
+            }
+        };
+        auto put_u = [&](int r, int col, C ux, C uy) {
+            C* u = uring + 2 * ((r & 3) * UW + col + 1);
+            u[0] = ux;
+            u[1] = uy;
+        };
+        auto moments_row = [&](int r, C (&d)[9], C& dR, C& jx, C& jy) {
+            // own column, then the two halo columns (threads 0 and 1)
+            if (r >= 0 && r < ny) {
+                C ux, uy;
+                pull(t, r, d);
+                gradient_velocity<C>(d, P.gx, dR, jx, jy, ux, uy);
+                put_u(r, t, ux, uy);
+                if (t == 32 || t == W - 32) {  // the two halo columns, on two different warps
+                    const int col = t == 32 ? -1 : W;
+                    C dh[9], hR, hx, hy;
+                    pull(col, r, dh);
+                    gradient_velocity<C>(dh, P.gx, hR, hx, hy, ux, uy);
+                    put_u(r, col, ux, uy);
+                }
+            }
+        };
+
+        // ---- prologue: copies of rows rbase .. rbase+K-1; rows rbase .. rbase+5 waited and patched;
+        // moments of rows y0-1, y0 (and of row 2 when the item starts at the bottom wall: the
+        // one-sided difference of row 0 needs it)
+        if (t == 0) {
+            fence_proxy_async();
+            for (int r = rbase; r < rbase + K && r <= rlast; ++r) issue(idx_of(r), x0, r);
+        }
+        nload = L0 + (uint32_t)(rlast - rbase + 1);
+        double r_du2 = 0.0, r_u2 = 0.0, r_ux = 0.0, r_umax2 = 0.0;  // residual partials (F_RESID)
+        C dcur[9], dnext[9];
+        C dRc = 0, jxc = 0, jyc = 0, dRn = 0, jxn = 0, jyn = 0;
+        bool ok = true;
+        for (int r = rbase; r <= rbase + 5; ++r) ok &= wait_row(r);
+        if (!ok) s_bad = 1;
+        T pv_a = T(0), pv_b = T(0);
+        if (patcher) {
+            for (int r = rbase; r <= rbase + 5; ++r) patch_store(r, patch_load(r));
+            pv_a = patch_load(y0 + 4);
+            pv_b = patch_load(y0 + 5);
+        }
+        __syncthreads();
+        if (s_bad) { bad = true; break; }
+        {
+            C dtmp[9], a0, a1, a2;
+            moments_row(y0 - 1, dtmp, a0, a1, a2);
+            if (y0 == 0) moments_row(2, dtmp, a0, a1, a2);
+        }
+        moments_row(y0, dcur, dRc, jxc, jyc);
+        // the stored flow-induced density, loaded two rows ahead of its use
+        C drho_next = a.drho[P.base + (long long)y0 * nx + x];
+        C drho_next2 = (y0 + 1 < y1) ? a.drho[P.base + (long long)(y0 + 1) * nx + x] : C(0);
+        __syncthreads();
+        if (t == 0) {
+            fence_proxy_async();
+            for (int r = rbase + K; r < rbase + K + 2 && r <= rlast; ++r) issue(idx_of(r), x0, r);
+        }
+
+        for (int y = y0; y < y1; ++y) {
+            // 1. moments of row y+1 (its own populations are the next row's collision input);
+            //    edge strips patch row y+4, which the moments of iteration y+2 read first
+            if (y + 2 <= rlast && !wait_row(y + 2)) s_bad = 1;
+            if (patcher && y + 4 <= rlast) {
+                if (!wait_row(y + 4)) s_bad = 1;
+                patch_store(y + 4, pv_a);
+                pv_a = pv_b;
+                pv_b = patch_load(y + 6);
+            }
+            moments_row(y + 1, dnext, dRn, jxn, jyn);
+            const C drho_prev = drho_next;
+            drho_next = drho_next2;
+            if (y + 2 < y1) drho_next2 = a.drho[P.base + (long long)(y + 2) * nx + x];
+            __syncthreads();
+            if (s_bad) { bad = true; break; }
+            // 2. refill the slot of row y (no longer read) with row y+K
+            if (t == 0 && y + K <= rlast) {
+                fence_proxy_async();
+                issue(idx_of(y + K), x0, y + K);
+            }
+            // 3. collision of row y
+            {
+                const C* uc = uring + 2 * ((y & 3) * UW + t + 1);
+                const C ka = C(0.5) * (uc[2] - uc[-2]);
+                const C kc = C(0.5) * (uc[3] - uc[-1]);
+                C kb, ke;
+                const C* up = uring + 2 * (((y + 1) & 3) * UW + t + 1);
+                const C* um = uring + 2 * (((y + 3) & 3) * UW + t + 1);  // row y-1
+                if (y == 0) {
+                    const C* up2 = uring + 2 * (((y + 2) & 3) * UW + t + 1);
+                    kb = C(0.5) * (C(-3) * uc[0] + C(4) * up[0] - up2[0]);
+                    ke = C(0.5) * (C(-3) * uc[1] + C(4) * up[1] - up2[1]);
+                } else if (y == ny - 1) {
+                    const C* um2 = uring + 2 * (((y + 2) & 3) * UW + t + 1);  // row y-2
+                    kb = C(0.5) * (C(3) * uc[0] - C(4) * um[0] + um2[0]);
+                    ke = C(0.5) * (C(3) * uc[1] - C(4) * um[1] + um2[1]);
+                } else {
+                    kb = C(0.5) * (up[0] - um[0]);
+                    ke = C(0.5) * (up[1] - um[1]);
+                }
+                C so_xx = 0, so_xy = 0, so_yy = 0;
+                const long long pn = (long long)y * nx + x;
+                if (SMODE == 1) {
+                    const C* s3 = a.sig3 + 3 * P.base;
+                    so_xx = s3[pn];
+                    so_xy = s3[P.P + pn];
+                    so_yy = s3[2 * P.P + pn];
+                }
+                const NodeState<C> s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dRc, jxc, jyc, drho_prev, so_xx, so_xy, so_yy);
+                const C rho_h = C(1) + s.dReq - s.drho;
+                if (!velocity_ok<C>(jxc, jyc, rho_h, a.guard)) atomicOr(a.status, 1);  // NaN or too fast
+                C D[9];
+                collide_node<C>(P, s, dcur, D);
+                T* po = a.pout + 9 * P.base + pn;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Store<T>::st(po + i * P.P, dcur[i] + D[i]);
+                a.drho[P.base + pn] = s.drho;
+                if (SMODE == 1) {
+                    C* s3 = a.sig3 + 3 * P.base;
+                    s3[pn] = s.sxx;
+                    s3[P.P + pn] = s.sxy;
+                    s3[2 * P.P + pn] = s.syy;
+                }
+                if (a.flags & F_STORE_SIGMA) {
+                    C* s4 = a.sig4 + 4 * P.base;
+                    s4[pn] = s.sxx;
+                    s4[P.P + pn] = s.syy;
+                    s4[2 * P.P + pn] = C(0);
+                    s4[3 * P.P + pn] = s.sxy;
+                }
+                if (a.flags & (F_SAVE_U | F_RESID)) {
+                    const C ih = Arith<C>::div(C(1), rho_h);
+                    const C urx = jxc * ih, ury = jyc * ih;
+                    C* up_ = a.uprev + 2 * P.base;
+                    if (a.flags & F_RESID) {
+                        const double dx_ = (double)urx - (double)up_[pn], dy_ = (double)ury - (double)up_[P.P + pn];
+                        const double u2 = (double)urx * urx + (double)ury * ury;
+                        r_du2 += dx_ * dx_ + dy_ * dy_;
+                        r_u2 += u2;
+                        r_ux += (double)urx;
+                        r_umax2 = fmax(r_umax2, u2);
+                    }
+                    if (a.flags & F_SAVE_U) {
+                        up_[pn] = urx;
+                        up_[P.P + pn] = ury;
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dcur[i] = dnext[i];
+            dRc = dRn; jxc = jxn; jyc = jyn;
+        }
+        __syncthreads();  // every slot read of this item is done before the next item's copies
+        if (!bad && (a.flags & F_RESID)) {
+            // block reduction of (sum du^2, sum u^2, sum u_x, max |u|) into this item's partials
+            double v[4] = {r_du2, r_u2, r_ux, r_umax2};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+                v[1] += __shfl_xor_sync(0xffffffffu, v[1], o);
+                v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
+                v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
+            }
+            double* red = reinterpret_cast<double*>(uring);  // the velocity ring is free now
+            if ((t & 31) == 0)
+                for (int k = 0; k < 4; ++k) red[4 * (t >> 5) + k] = v[k];
+            __syncthreads();
+            if (t == 0) {
+                double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                for (int w = 0; w < W / 32; ++w) {
+                    s0 += red[4 * w]; s1 += red[4 * w + 1]; s2 += red[4 * w + 2]; s3 = fmax(s3, red[4 * w + 3]);
+                }
+                double* o = a.partials + 4 * (long long)item;
+                o[0] = s0; o[1] = s1; o[2] = s2; o[3] = sqrt(s3);
+            }
+            __syncthreads();
+        }
+    }
+
+    if (bad) {
+        // record the timeout and drain this CTA's own copies (bounded) before leaving
+        if (t == 0) {
+            atomicOr(ctl.timeout_flag, 2);
+            for (int k = 0; k < K; ++k)
+                if (last_issued[k] != 0xffffffffu) mbar_wait(&bars[k], (last_issued[k] / K) & 1u, 100000000ull);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace lbk
+
+namespace lbk {
+constexpr int kMarchW = 128;  // threads (= columns) per CTA
+constexpr int kMarchK = 8;    // shared-memory row slots (copies run K-2 rows ahead)
+
+template <typename T, typename C, int SMODE>
+cudaError_t launch_step_march(const CUtensorMap& map, const StepArgs<T, C>& a, const MarchCtl& ctl, int grid,
+                              cudaStream_t s) {
+    auto k = k_step_march<T, C, SMODE, kMarchW, kMarchK>;
+    const size_t smem = march_smem_bytes<T, C, kMarchW, kMarchK>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kMarchW, smem, s>>>(map, a, ctl);
+    return cudaGetLastError();
+}
+
+template <typename T, typename C, int SMODE>
+cudaError_t march_occupancy(int* blocks_per_sm) {
+    auto k = k_step_march<T, C, SMODE, kMarchW, kMarchK>;
+    const size_t smem = march_smem_bytes<T, C, kMarchW, kMarchK>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kMarchW, smem);
+}
+}  // namespace lbk

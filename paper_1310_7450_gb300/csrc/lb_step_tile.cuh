@@ -143,9 +143,13 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
 
         // reported fields: hydrodynamic density rho_eq - delta rho (Eq. rhoj), u = j / rho
         const C rho_h = C(1) + s.dReq - s.drho;
-        const C urx = jx / rho_h, ury = jy / rho_h;
-        const C umag = csqrt<C>(urx * urx + ury * ury);
-        if (!(umag <= a.guard)) atomicOr(a.status + it.ch, 1);  // NaN or too fast
+        if (!velocity_ok<C>(jx, jy, rho_h, a.guard)) atomicOr(a.status + it.ch, 1);  // NaN or too fast
+        C urx = C(0), ury = C(0);
+        if (a.flags & (F_FIELDS | F_SAVE_U | F_RESID)) {
+            const C ih = Arith<C>::div(C(1), rho_h);
+            urx = jx * ih;
+            ury = jy * ih;
+        }
 
         if (a.flags & F_FIELDS) {
             const long long node = P.node_off + pn;
@@ -157,21 +161,11 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
             a.fsig[4 * node + 3] = s.sxy;
             a.frho[node] = rho_h;
         } else {
-            const C usq = s.ux * s.ux + s.uy * s.uy;
-            // the tensor multiplying Q_i in Eq. (bodyforce): -S u u + u f + f u, f = (gx, 0)
-            const C Yxx = -s.S * s.ux * s.ux + C(2) * s.ux * P.gx;
-            const C Yyy = -s.S * s.uy * s.uy;
-            const C Yxy = -s.S * s.ux * s.uy + s.uy * P.gx;
+            C D[9];
+            collide_node<C>(P, s, d, D);
             T* po = a.pout + 9 * P.base + pn;
-            Store<T>::st(po + 0 * P.P, collide_dir<C, 0>(P, s, d[0], usq, Yxx, Yyy, Yxy));
-            Store<T>::st(po + 1 * P.P, collide_dir<C, 1>(P, s, d[1], usq, Yxx, Yyy, Yxy));
-            Store<T>::st(po + 2 * P.P, collide_dir<C, 2>(P, s, d[2], usq, Yxx, Yyy, Yxy));
-            Store<T>::st(po + 3 * P.P, collide_dir<C, 3>(P, s, d[3], usq, Yxx, Yyy, Yxy));
-            Store<T>::st(po + 4 * P.P, collide_dir<C, 4>(P, s, d[4], usq, Yxx, Yyy, Yxy));
-            Store<T>::st(po + 5 * P.P, collide_dir<C, 5>(P, s, d[5], usq, Yxx, Yyy, Yxy));
-            Store<T>::st(po + 6 * P.P, collide_dir<C, 6>(P, s, d[6], usq, Yxx, Yyy, Yxy));
-            Store<T>::st(po + 7 * P.P, collide_dir<C, 7>(P, s, d[7], usq, Yxx, Yyy, Yxy));
-            Store<T>::st(po + 8 * P.P, collide_dir<C, 8>(P, s, d[8], usq, Yxx, Yyy, Yxy));
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Store<T>::st(po + i * P.P, d[i] + D[i]);
             dr[pn] = s.drho;
             if (SMODE == 1) {
                 C* s3 = a.sig3 + 3 * P.base;
@@ -194,7 +188,7 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
                 res_du2 = dx_ * dx_ + dy_ * dy_;
                 res_u2 = urx * urx + ury * ury;
                 res_ux = urx;
-                res_umax = umag;
+                res_umax = Arith<C>::sqrt(res_u2);
             }
             if (a.flags & F_SAVE_U) {
                 up[pn] = urx;

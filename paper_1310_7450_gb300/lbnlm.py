@@ -21,8 +21,10 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbnlm.so
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = range(7)
 LB_PREC_F64, LB_PREC_F32, LB_PREC_BF16 = 0, 1, 2
 LB_STRESS_INLM, LB_STRESS_TIMESTEPPED = 0, 1
-LB_GRID_STORE_SIGMA = 1
-PRECISIONS = {"f64": LB_PREC_F64, "f32": LB_PREC_F32, "bf16": LB_PREC_BF16}
+LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY = 1, 2
+LB_PREC_F64S_F32M, LB_PREC_F32S_F64M = 3, 4
+PRECISIONS = {"f64": LB_PREC_F64, "f32": LB_PREC_F32, "bf16": LB_PREC_BF16, "f64s_f32m": LB_PREC_F64S_F32M,
+              "f32s_f64m": LB_PREC_F32S_F64M}
 
 
 class lb_grid(ctypes.Structure):
@@ -74,6 +76,7 @@ def load():
         "lb_set_state": ([_H, c_void_p, c_size_t], c_int),
         "lb_channel_status": ([_H, POINTER(c_int)], c_int),
         "lb_step_count": ([_H], c_long),
+        "lb_uses_row_march": ([_H], c_int),
         "lb_num_nodes": ([_H], c_size_t),
         "lb_destroy": ([_H], None),
         "lb_strerror": ([c_int], ctypes.c_char_p),
@@ -190,6 +193,10 @@ def lb_channel_status(h: int, out: np.ndarray):
 
 def lb_step_count(h: int) -> int:
     return int(load().lb_step_count(h))
+
+
+def lb_uses_row_march(h: int) -> bool:
+    return bool(load().lb_uses_row_march(h))
 
 
 def lb_num_nodes(h: int) -> int:

@@ -128,7 +128,7 @@ def random_state(oracle_mod, nx, ny, seed, amp=1e-3):
     rng = np.random.default_rng(seed)
     st = oracle_mod.init_state(1.0 + amp * rng.uniform(-1, 1, (ny, nx)))
     w = oracle_mod.equilibrium(1.0, 0.0, 0.0)
-    st.nstar += amp * rng.uniform(-1, 1, st.nstar.shape) * w[:, None, None]
+    st.dev += amp * rng.uniform(-1, 1, st.dev.shape) * w[:, None, None]
     st.drho[:] = 1e-2 * amp * rng.uniform(-1, 1, (ny, nx))
     return st
 

@@ -171,3 +171,14 @@ def test_time_stepped_stress_fixed_point(oracle_mod):
         for _ in range(int(60 * tau_M) + 200):
             s = oracle_mod.stress_step(kap, tau_M, 1e-3, s)
         np.testing.assert_allclose(s, s_ss, rtol=1e-10, atol=1e-12 * np.abs(s_ss).max())
+
+
+def test_equilibrium_offset_form(oracle_mod):
+    """The offset form used by the stepping equals Eq. (neq) minus the weights."""
+    rng = np.random.default_rng(15)
+    for _ in range(50):
+        rho = 1.0 + 0.05 * rng.uniform(-1, 1)
+        u = 0.1 * rng.uniform(-1, 1, 2)
+        full = oracle_mod.equilibrium(rho, u[0], u[1]) - oracle_mod.WEIGHTS
+        off = oracle_mod.equilibrium_offset(rho - 1.0, u[0], u[1])
+        np.testing.assert_allclose(off, full, rtol=0, atol=2e-16)
