@@ -150,6 +150,22 @@ lb_status lb_set_state(lb_handle *h, const void *buf, size_t bytes);
  * |u| > 0.3; the channel is retired); bit 2 = a bounded device-side wait timed out. */
 lb_status lb_channel_status(lb_handle *h, int *status);
 
+/* Allocation-free diagnostics.  The paper has no counterpart: this is a service for callers that
+ * must not allocate device memory when they ask for the convergence measures -- e.g. a monitoring
+ * loop that cannot take cudaMalloc's implicit device synchronisation mid-run, or a process whose
+ * device memory is fully reserved by another allocator.  From two velocity fields on the device
+ * (u_now, u_prev: [node][2], dtype 0 = double, 1 = float, node order as lb_get_fields) and the
+ * channel boundaries node_offsets (device, [n_channels + 1], long long), it writes per channel
+ * (residual ||u_now - u_prev||_2/||u_now||_2, flux = sum of u_x / nx, max |u|) to out (device,
+ * [n_channels][3], double), on cuda_stream.  It calls no allocating routine: its scratch is a fixed
+ * 2 MiB array inside the library (65536 records; at most 1024 channels per call, larger requests
+ * fail with LB_EINVAL) that every GPU using the library keeps until the process exits.  The first
+ * call on a device looks the array up (cudaGetSymbolAddress); make that call before any stream
+ * capture.  Calls share the array, so calls that overlap on the GPU (e.g. on two streams) race;
+ * each call writes every scratch record it reads, so nothing needs clearing between calls. */
+lb_status lb_field_monitor_static(const void *u_now, const void *u_prev, int dtype, int n_channels,
+                                  const long long *node_offsets, int nx, double *out, void *cuda_stream);
+
 long lb_step_count(const lb_handle *h);     /* steps taken since creation (or restored)      */
 int lb_uses_row_march(const lb_handle *h);  /* 1 if plain steps run on the row-march kernel   */
 size_t lb_num_nodes(const lb_handle *h);     /* total fluid nodes over all channels           */

@@ -52,6 +52,15 @@ lb_status fail(lb_status s, const char* fmt, const char* detail = nullptr) {
     std::snprintf(g_err, sizeof g_err, fmt, detail ? detail : "");
     return s;
 }
+}  // namespace
+
+namespace lbk {
+// Lets other translation units of the library report a failure through lb_last_error().
+void set_last_error(const char* msg) { std::snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace lbk
+
+namespace {
+
 lb_status cuda_fail(cudaError_t e, const char* where) {
     std::snprintf(g_err, sizeof g_err, "%s: %s", where, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;

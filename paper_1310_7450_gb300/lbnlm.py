@@ -76,6 +76,7 @@ def load():
         "lb_set_state": ([_H, c_void_p, c_size_t], c_int),
         "lb_channel_status": ([_H, POINTER(c_int)], c_int),
         "lb_step_count": ([_H], c_long),
+        "lb_field_monitor_static": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p], c_int),
         "lb_uses_row_march": ([_H], c_int),
         "lb_num_nodes": ([_H], c_size_t),
         "lb_destroy": ([_H], None),
@@ -189,6 +190,12 @@ def lb_set_state(h: int, buf: np.ndarray):
 def lb_channel_status(h: int, out: np.ndarray):
     assert out.dtype == np.int32
     _check(load().lb_channel_status(h, out.ctypes.data_as(POINTER(c_int))), "lb_channel_status")
+
+
+def lb_field_monitor_static(u_now, u_prev, dtype: int, n_channels: int, node_offsets, nx: int, out, stream=None):
+    """Device tensors in, device tensor out (see include/lbnlm.h); allocates nothing."""
+    _check(load().lb_field_monitor_static(_ptr(u_now), _ptr(u_prev), int(dtype), int(n_channels), _ptr(node_offsets),
+                                          int(nx), _ptr(out), c_void_p(stream or 0)), "lb_field_monitor_static")
 
 
 def lb_step_count(h: int) -> int:
