@@ -303,6 +303,67 @@ def run_gpu(args):
     return 0
 
 
+def run_sweep(args):
+    """Batched sweep: the 512-channel draw (Nx = 4, Ny ~ U{32..1024}, g = b (32/Ny)^2 with
+    b ~ logU[1e-8, 1e-5], theta = 10^(2 + 10 eps), eps ~ U[-0.1, 0.1], seed 3), FP32, all channels
+    from rest to a one-step residual <= tol in one persistent launch.  Baseline: the plain
+    per-channel scheme (one single-channel handle per channel, lb_step in chunks of `check` steps
+    and lb_residual between chunks); its time per step is measured on a stratified sample of
+    channels and multiplied by each channel's own step count (the same steps as in the sweep)."""
+    import torch
+    from paper_1310_7450_gb300 import build as libbuild
+    from paper_1310_7450_gb300 import inputs, lbnlm
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    libbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    params = inputs.sweep_channel_params(args.channels, args.sweep_seed)
+    nys = [q.pop("ny") for q in params]
+    sim = lbnlm.Channels(4, nys, params, args.precision, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    lbnlm.lb_sweep_tune(sim.h)
+    tune_s = time.perf_counter() - t0
+    nt, cl, tune_ms = lbnlm.lb_sweep_config(sim.h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, res = sim.run_until_steady(args.tol, check_every=args.check, max_steps=args.max_steps)
+    wall = time.perf_counter() - t0
+    sim.close()
+    conv = steps > 0
+    # plain per-channel baseline on a stratified sample (by width)
+    order = np.argsort(nys)
+    sample = order[np.linspace(0, len(order) - 1, args.baseline_sample).astype(int)]
+    per_step = {}
+    for c in sample:
+        one = lbnlm.Channels(4, nys[c], params[c], args.precision, stream=stream.cuda_stream)
+        one.step(args.check)
+        torch.cuda.synchronize()
+        n_chunks = max(2, args.baseline_steps // args.check)
+        t1 = time.perf_counter()
+        for _ in range(n_chunks):
+            one.step(args.check)
+            one.residual()
+        per_step[int(c)] = (time.perf_counter() - t1) / (n_chunks * args.check)
+        one.close()
+    xs = np.array([nys[c] for c in per_step]); ys = np.array([per_step[c] for c in per_step])
+    fit = np.polyfit(xs, ys, 1)          # seconds per step as a function of Ny (launch-bound: ~flat)
+    est = float(sum(max(steps[c], 0) * np.polyval(fit, nys[c]) for c in range(len(nys))))
+    line = {"metric": "batched-sweep time-to-steady (plain per-channel vs one persistent launch)",
+            "value": wall, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": args.precision,
+            "data": "synthetic", "config": {"workload": f"{len(nys)} channels, Nx=4, Ny~U{{32..1024}}, seed {args.sweep_seed}",
+                                            "tol": args.tol, "check_every": args.check, "max_steps": args.max_steps},
+            "converged": int(conv.sum()), "channels": len(nys), "max_steps_taken": int(steps.max()),
+            "steps_percentiles": [int(v) for v in np.percentile(steps[conv], [0, 50, 90, 100])] if conv.any() else None,
+            "node_steps": int(sum(max(steps[c], 0) * 4 * nys[c] for c in range(len(nys)))),
+            "autotune": {"threads": nt, "cluster": cl, "tune_run_ms": tune_ms, "tune_wall_s": tune_s},
+            "baseline_plain_per_channel": {"estimated_s": est, "sample_channels": len(per_step),
+                                           "per_step_us_by_ny": {str(nys[c]): round(1e6 * v, 2) for c, v in per_step.items()}},
+            "speedup_vs_plain": est / wall if wall > 0 else None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,7 +380,17 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-crop", type=int, default=256)
+    ap.add_argument("--workload", default="channel", choices=["channel", "sweep"])
+    ap.add_argument("--channels", type=int, default=512)
+    ap.add_argument("--sweep-seed", type=int, default=3)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--check", type=int, default=100)
+    ap.add_argument("--max-steps", type=int, default=20_000_000)
+    ap.add_argument("--baseline-sample", type=int, default=8)
+    ap.add_argument("--baseline-steps", type=int, default=2000)
     args = ap.parse_args()
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

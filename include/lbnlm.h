@@ -150,6 +150,23 @@ lb_status lb_set_state(lb_handle *h, const void *buf, size_t bytes);
  * |u| > 0.3; the channel is retired); bit 2 = a bounded device-side wait timed out. */
 lb_status lb_channel_status(lb_handle *h, int *status);
 
+/* Batched sweep: step every stable channel until its one-step residual ||u(t)-u(t-1)||/||u(t)|| is
+ * <= tol, checked every check_every steps (even, >= 2), or until max_steps (rounded up to a multiple
+ * of check_every).  ONE persistent launch: each channel is owned by a thread-block cluster that runs
+ * its own time loop (hardware cluster barrier per step) and leaves when the channel has converged;
+ * the widest channels start first.  The first call tunes the CTA size and the cluster size by timing
+ * short sweeps from the current state (the state is restored) -- see lb_sweep_config.  Outputs
+ * (host, [n_channels], may be NULL): steps taken (-1: max_steps reached, -2: unstable) and the last
+ * residual.  Each channel advances by its own number of steps; lb_step_count() is not changed.
+ * Stress mode 0 only.  Synchronises the stream. */
+lb_status lb_run_until_steady(lb_handle *h, double tol, long check_every, long max_steps, long long *steps_out,
+                              double *residual_out);
+/* Run the sweep autotuner now (otherwise the first lb_run_until_steady does); the state is kept. */
+lb_status lb_sweep_tune(lb_handle *h);
+/* The sweep configuration chosen by the autotuner (0 before the first sweep) and the time of its
+ * tuning run (ms for 256 steps of every channel). */
+lb_status lb_sweep_config(lb_handle *h, int *threads, int *cluster, double *tune_ms);
+
 /* Allocation-free diagnostics.  The paper has no counterpart: this is a service for callers that
  * must not allocate device memory when they ask for the convergence measures -- e.g. a monitoring
  * loop that cannot take cudaMalloc's implicit device synchronisation mid-run, or a process whose

@@ -15,10 +15,12 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "lb_step_march.cuh"
 #include "lb_step_tile.cuh"
+#include "lb_sweep.cuh"
 #include "lbnlm.h"
 
 namespace lbk {
@@ -36,6 +38,13 @@ extern template cudaError_t launch_step_march<float, float, 0>(const CUtensorMap
 extern template cudaError_t launch_step_march<float, float, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t launch_step_march<__nv_bfloat16, float, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+#define LB_SWEEP_EXTERN(T, C)                                                                                   \
+    extern template cudaError_t launch_sweep<T, C, 128, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_sweep<T, C, 256, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t);
+LB_SWEEP_EXTERN(float, float)
+LB_SWEEP_EXTERN(__nv_bfloat16, float)
+LB_SWEEP_EXTERN(double, double)
+#undef LB_SWEEP_EXTERN
 extern template cudaError_t march_occupancy<float, float, 0>(int*);
 extern template cudaError_t march_occupancy<float, float, 1>(int*);
 extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0>(int*);
@@ -290,6 +299,12 @@ struct lb_handle {
     CUtensorMap mapA, mapB;    // tensor maps of the two population buffers ...
     const void* mapA_buf = nullptr;  // ... and the buffers they describe (the pointers swap)
     const void* mapB_buf = nullptr;
+    // persistent cluster sweep
+    long long* sweep_steps_d = nullptr;
+    double* sweep_res_d = nullptr;
+    int* sweep_order_d = nullptr;
+    int sweep_nt = 0, sweep_cl = 0;     // tuned configuration (0: not tuned yet)
+    double sweep_tune_ms = 0.0;
     MarchItem* march_items_d = nullptr;
     int* march_item_begin_d = nullptr;  // {0, n_march_items}: the residual reduction's item range
     int n_march_items = 0, march_grid = 0;
@@ -482,6 +497,9 @@ void release(lb_handle* h) {
     free_dev(h->hstage);
     free_dev(h->march_items_d);
     free_dev(h->march_item_begin_d);
+    free_dev(h->sweep_steps_d);
+    free_dev(h->sweep_res_d);
+    free_dev(h->sweep_order_d);
     if (h->status_h) cudaFreeHost(h->status_h);
     if (h->gx_h) cudaFreeHost(h->gx_h);
     if (h->status_ev) cudaEventDestroy(h->status_ev);
@@ -600,11 +618,180 @@ lb_status request_status(lb_handle* h) {
     return LB_OK;
 }
 
+constexpr int kSweepNPT = 4;  // nodes per thread of the sweep kernel
+
+int sweep_max_ny(const lb_handle* h) {
+    int m = 0;
+    for (int c = 0; c < h->n_ch; ++c) m = std::max(m, h->ny[c]);
+    return m;
+}
+bool sweep_fits(const lb_handle* h, int nt, int cl) {
+    const int rows = (sweep_max_ny(h) + cl - 1) / cl;
+    return (long long)rows * h->nx <= (long long)nt * kSweepNPT;
+}
+size_t sweep_smem(const lb_handle* h, int cl) {
+    const int rows = (sweep_max_ny(h) + cl - 1) / cl + 4;
+    return (size_t)rows * h->nx * 2 * h->csize;
+}
+
+template <typename T, typename C>
+cudaError_t sweep_launch(lb_handle* h, int nt, int cl, int n_clusters, double tol, int check, long long max_steps) {
+    SweepArgs<T, C> a{};
+    a.popA = (T*)h->popA;
+    a.popB = (T*)h->popB;
+    a.drho = (C*)h->drho;
+    a.uprev = (C*)h->uprev;
+    a.chan = (const ChanParams<C>*)h->chan;
+    a.status = h->status_d;
+    a.order = h->sweep_order_d;
+    a.steps_out = h->sweep_steps_d;
+    a.res_out = h->sweep_res_d;
+    a.nx = h->nx;
+    a.check = check;
+    a.max_steps = max_steps;
+    a.tol = tol;
+    const size_t smem = sweep_smem(h, cl);
+    if (nt == 128) return launch_sweep<T, C, 128, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
+    return launch_sweep<T, C, 256, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
+}
+
+cudaError_t sweep_launch_any(lb_handle* h, int nt, int cl, int n_clusters, double tol, int check, long long max_steps) {
+    return with_types(h->prec, [&](auto tt, auto tc) -> cudaError_t {
+        LB_TYPES(tt, tc);
+        if constexpr (std::is_same<T, double>::value != std::is_same<C, double>::value) return cudaErrorNotSupported;
+        else return sweep_launch<T, C>(h, nt, cl, n_clusters, tol, check, max_steps);
+    });
+}
+
+// Stable channels, widest first (the longest-running clusters start first).
+lb_status sweep_order(lb_handle* h, int* n_active) {
+    std::vector<int> st(h->n_ch);
+    LB_CK(cudaMemcpyAsync(st.data(), h->status_d, sizeof(int) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    std::vector<int> order;
+    for (int c = 0; c < h->n_ch; ++c)
+        if (st[c] == 0) order.push_back(c);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->ny[a] > h->ny[b]; });
+    if (!h->sweep_order_d) {
+        LB_CK(cudaMalloc(&h->sweep_order_d, sizeof(int) * h->n_ch));
+        LB_CK(cudaMalloc(&h->sweep_steps_d, sizeof(long long) * h->n_ch));
+        LB_CK(cudaMalloc(&h->sweep_res_d, sizeof(double) * h->n_ch));
+    }
+    if (!order.empty())
+        LB_CK(cudaMemcpy(h->sweep_order_d, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
+    *n_active = (int)order.size();
+    return LB_OK;
+}
+
+// Autotuner: time a short sweep (no channel can converge: tol < 0) for every (threads, cluster
+// size) that fits, from the same saved state, and keep the fastest.  The state is restored.
+lb_status sweep_tune(lb_handle* h, int n_active) {
+    struct Cand { int nt, cl; };
+    std::vector<Cand> cands;
+    for (int nt : {128, 256})
+        for (int cl : {1, 2, 4, 8, 16})
+            if (sweep_fits(h, nt, cl) && sweep_smem(h, cl) <= 200 * 1024) cands.push_back({nt, cl});
+    if (cands.empty()) return fail(LB_EINVAL, "lb_run_until_steady: a channel is too wide for the sweep kernel%s");
+    const size_t pop_b = 9 * h->planes * h->tsize, dr_b = h->planes * h->csize, up_b = 2 * h->planes * h->csize;
+    void* save = nullptr;
+    LB_CK(cudaMalloc(&save, pop_b + dr_b + up_b));
+    char* sv = (char*)save;
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(h->popA, sv, pop_b, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->drho, sv + pop_b, dr_b, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->uprev, sv + pop_b + dr_b, up_b, cudaMemcpyDeviceToDevice, h->stream);
+        return e;
+    };
+    cudaError_t e = cudaMemcpyAsync(sv, h->popA, pop_b, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv + pop_b, h->drho, dr_b, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv + pop_b + dr_b, h->uprev, up_b, cudaMemcpyDeviceToDevice, h->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = 1e300;
+    for (const Cand& c : cands) {
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
+            e = restore();
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+            if (e == cudaSuccess) e = sweep_launch_any(h, c.nt, c.cl, n_active, -1.0, 16, 256);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            h->sweep_nt = c.nt;
+            h->sweep_cl = c.cl;
+        }
+    }
+    if (e == cudaSuccess) e = restore();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (e != cudaSuccess) { h->sweep_nt = h->sweep_cl = 0; return cuda_fail(e, "lb_run_until_steady: autotune"); }
+    h->sweep_tune_ms = best;
+    return LB_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char* lb_last_error(void) { return g_err; }
+
+lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long max_steps, long long* steps_out,
+                              double* residual_out) {
+    if (!h || check_every < 2 || (check_every & 1) || max_steps < check_every || std::isnan(tol))
+        return fail(LB_EINVAL, "lb_run_until_steady: need an even check_every >= 2 and max_steps >= check_every%s");
+    if (h->smode != 0) return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements stress mode 0%s");
+    if (h->prec == LB_PREC_F64S_F32M || h->prec == LB_PREC_F32S_F64M)
+        return fail(LB_EINVAL, "lb_run_until_steady: diagnostic precision mixes are not supported%s");
+    int n_active = 0;
+    lb_status st = sweep_order(h, &n_active);
+    if (st != LB_OK) return st;
+    const long long ms = (long long)((max_steps + check_every - 1) / check_every) * check_every;
+    std::vector<long long> steps(h->n_ch, 0);
+    std::vector<double> res(h->n_ch, NAN);
+    if (n_active > 0) {
+        if (!h->sweep_nt) {
+            st = sweep_tune(h, n_active);
+            if (st != LB_OK) return st;
+        }
+        std::vector<long long> init(h->n_ch, -3);
+        LB_CK(cudaMemcpy(h->sweep_steps_d, init.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice));
+        LB_CK(sweep_launch_any(h, h->sweep_nt, h->sweep_cl, n_active, tol, (int)check_every, ms));
+        LB_CK(cudaMemcpyAsync(steps.data(), h->sweep_steps_d, sizeof(long long) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
+        LB_CK(cudaMemcpyAsync(res.data(), h->sweep_res_d, sizeof(double) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
+        LB_CK(cudaStreamSynchronize(h->stream));
+    }
+    for (int c = 0; c < h->n_ch; ++c) {
+        if (steps_out) steps_out[c] = steps[c] == -3 ? -2 : steps[c];  // -3: not in the sweep (unstable before)
+        if (residual_out) residual_out[c] = res[c];
+    }
+    h->uprev_state = -10;
+    h->mon_state = -1;
+    return LB_OK;
+}
+
+lb_status lb_sweep_tune(lb_handle* h) {
+    if (!h) return fail(LB_EINVAL, "lb_sweep_tune: null handle%s");
+    if (h->smode != 0) return fail(LB_EINVAL, "lb_sweep_tune: the sweep kernel implements stress mode 0%s");
+    int n_active = 0;
+    lb_status st = sweep_order(h, &n_active);
+    if (st != LB_OK || n_active == 0) return st;
+    return sweep_tune(h, n_active);
+}
+
+lb_status lb_sweep_config(lb_handle* h, int* threads, int* cluster, double* tune_ms) {
+    if (!h) return fail(LB_EINVAL, "lb_sweep_config: null handle%s");
+    if (threads) *threads = h->sweep_nt;
+    if (cluster) *cluster = h->sweep_cl;
+    if (tune_ms) *tune_ms = h->sweep_tune_ms;
+    return LB_OK;
+}
 
 const char* lb_strerror(lb_status s) {
     switch (s) {

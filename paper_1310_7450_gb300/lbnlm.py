@@ -76,6 +76,9 @@ def load():
         "lb_set_state": ([_H, c_void_p, c_size_t], c_int),
         "lb_channel_status": ([_H, POINTER(c_int)], c_int),
         "lb_step_count": ([_H], c_long),
+        "lb_run_until_steady": ([_H, c_double, c_long, c_long, c_void_p, c_void_p], c_int),
+        "lb_sweep_config": ([_H, POINTER(c_int), POINTER(c_int), POINTER(c_double)], c_int),
+        "lb_sweep_tune": ([_H], c_int),
         "lb_field_monitor_static": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p], c_int),
         "lb_uses_row_march": ([_H], c_int),
         "lb_num_nodes": ([_H], c_size_t),
@@ -198,6 +201,24 @@ def lb_field_monitor_static(u_now, u_prev, dtype: int, n_channels: int, node_off
                                           int(nx), _ptr(out), c_void_p(stream or 0)), "lb_field_monitor_static")
 
 
+def lb_run_until_steady(h: int, tol: float, check_every: int, max_steps: int, steps_out=None, residual_out=None):
+    """steps_out: int64 [n_channels], residual_out: float64 [n_channels] (host NumPy, optional)."""
+    if steps_out is not None:
+        assert steps_out.dtype == np.int64
+    _check(load().lb_run_until_steady(h, float(tol), int(check_every), int(max_steps), _ptr(steps_out),
+                                      _ptr(residual_out)), "lb_run_until_steady")
+
+
+def lb_sweep_tune(h: int):
+    _check(load().lb_sweep_tune(h), "lb_sweep_tune")
+
+
+def lb_sweep_config(h: int):
+    nt, cl, ms = c_int(), c_int(), c_double()
+    _check(load().lb_sweep_config(h, ctypes.byref(nt), ctypes.byref(cl), ctypes.byref(ms)), "lb_sweep_config")
+    return nt.value, cl.value, ms.value
+
+
 def lb_step_count(h: int) -> int:
     return int(load().lb_step_count(h))
 
@@ -290,6 +311,13 @@ class Channels:
         if sig3s is not None:
             s = np.concatenate([np.ascontiguousarray(x, dtype=np.float64).reshape(-1) for x in sig3s])
         lb_set_populations(self.h, n, d, s)
+
+    def run_until_steady(self, tol, check_every=100, max_steps=10**7):
+        """Per channel (steps, residual) of the persistent sweep."""
+        steps = np.zeros(len(self.ny), dtype=np.int64)
+        res = np.zeros(len(self.ny))
+        lb_run_until_steady(self.h, tol, check_every, max_steps, steps, res)
+        return steps, res
 
     def monitor(self):
         m = np.zeros(4 * len(self.ny))

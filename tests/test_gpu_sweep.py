@@ -1,0 +1,92 @@
+"""The persistent cluster sweep (lb_run_until_steady) against the oracle and against lb_step."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_7450_gb300 import inputs, lbnlm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+def rel(a, b):
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def channel_set(nys, seed):
+    ps = []
+    for k, ny in enumerate(nys):
+        theta = [0.0, 10.0, 100.0][k % 3]
+        G = inputs.nu_lb(0.9) / (50.0 * (1 + theta))
+        ps.append(dict(inputs.matched_params(0.9, theta, 0.1, G, 3e-6 * (16.0 / ny) ** 2), rho_pert_amp=1e-4,
+                       seed=seed + k))
+    return ps
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_sweep_fixed_steps_matches_oracle(stream, prec, tol):
+    """tol < 0: no channel converges, each runs exactly max_steps."""
+    nys = [3, 5, 16, 37, 64, 130]
+    ps = channel_set(nys, 40)
+    steps = 300
+    with lbnlm.Channels(4, nys, ps, prec, stream=stream) as sim:
+        st_, res = sim.run_until_steady(-1.0, check_every=20, max_steps=steps)
+        assert list(st_) == [-1] * len(nys)
+        fields = sim.fields()
+        nt, cl, _ = lbnlm.lb_sweep_config(sim.h)
+        assert nt in (128, 256) and cl in (1, 2, 4, 8, 16)
+    for k, (ny, p) in enumerate(zip(nys, ps)):
+        st = oracle.init_state(inputs.initial_density(4, ny, 1.0, 1e-4, 40 + k))
+        oracle.run(p, st, steps)
+        u_o, s_o, _ = oracle.fields(p, st)
+        u_g, s_g, _ = fields[k]
+        assert rel(u_g, u_o) < tol, (ny, rel(u_g, u_o))
+
+
+def test_sweep_equals_lb_step(stream):
+    nys = [24, 80]
+    ps = channel_set(nys, 50)
+    with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as a, lbnlm.Channels(4, nys, ps, "f64", stream=stream) as b:
+        a.run_until_steady(-1.0, check_every=10, max_steps=200)
+        b.step(200)
+        pa, pb = a.populations(), b.populations()
+    for k in range(2):
+        assert rel(pa[k][0], pb[k][0]) < 1e-14
+
+
+def test_sweep_converges_and_reports_steps(stream):
+    nys = [12, 20, 28]
+    ps = [dict(inputs.matched_params(0.9, 0.0, 0.1, 1e-3, 1e-6)) for _ in nys]
+    with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim:
+        steps, res = sim.run_until_steady(1e-8, check_every=50, max_steps=10**6)
+        assert np.all(steps > 0) and np.all(res <= 1e-8)
+        # wider channels take longer (diffusion time ~ H^2 / nu)
+        assert steps[0] < steps[1] < steps[2]
+        # the state is (close to) the Newtonian steady parabola
+        fl = sim.fields()
+    from oracle import analytic
+    for k, ny in enumerate(nys):
+        par = analytic.newtonian_parabola(ny, 1e-6, inputs.nu_lb(0.9))
+        assert np.abs(fl[k][0][:, 0, 0] - par).max() < 2e-3 * par.max()
+
+
+def test_sweep_retires_unstable_channel(stream):
+    nys = [16, 16]
+    ps = channel_set(nys, 60)
+    with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim:
+        pops = sim.populations()
+        n1 = pops[1][0].copy()
+        n1[2, 4, 1] = np.nan
+        sim.set_populations([pops[0][0], n1], [pops[0][1], pops[1][1]])
+        steps, res = sim.run_until_steady(-1.0, check_every=10, max_steps=100)
+        status = sim.status()
+    assert steps[0] == -1 and steps[1] == -2
+    assert list(status) == [0, 1]
