@@ -150,9 +150,11 @@ lb_status lb_set_state(lb_handle *h, const void *buf, size_t bytes);
  * |u| > 0.3; the channel is retired); bit 2 = a bounded device-side wait timed out. */
 lb_status lb_channel_status(lb_handle *h, int *status);
 
-/* Batched sweep: step every stable channel until its one-step residual ||u(t)-u(t-1)||/||u(t)|| is
- * <= tol, checked every check_every steps (even, >= 2), or until max_steps (rounded up to a multiple
- * of check_every).  ONE persistent launch: each channel is owned by a thread-block cluster that runs
+/* Batched sweep: step every stable channel until its residual over the check interval k,
+ * ||u(t) - u(t-k)|| / (k ||u(t)||), is <= tol, checked every k = check_every steps (even, >= 2), or
+ * until max_steps (rounded up to a multiple of k).  Over one step that change sits on the FP32
+ * rounding floor of a steady state; over k steps the floor falls as 1/k while a smooth exponential
+ * approach to the steady state gives the one-step value.  ONE persistent launch: each channel is owned by a thread-block cluster that runs
  * its own time loop (hardware cluster barrier per step) and leaves when the channel has converged;
  * the widest channels start first.  The first call tunes the CTA size and the cluster size by timing
  * short sweeps from the current state (the state is restored) -- see lb_sweep_config.  Outputs
@@ -182,6 +184,23 @@ lb_status lb_sweep_config(lb_handle *h, int *threads, int *cluster, double *tune
  * each call writes every scratch record it reads, so nothing needs clearing between calls. */
 lb_status lb_field_monitor_static(const void *u_now, const void *u_prev, int dtype, int n_channels,
                                   const long long *node_offsets, int nx, double *out, void *cuda_stream);
+
+/* ---- Learned warm start (not in the paper): a three-layer perceptron n_in -> width -> width ->
+ * n_out (tanh hidden layers) with BF16 working weights, FP32 master weights and FP32 accumulation,
+ * trained with Adam on a mean-squared-error loss by this library's kernels.  Parameters are flat
+ * FP32 in the order W1 [width][n_in], b1, W2 [width][width], b2, W3 [n_out][width], b3.  Arrays x
+ * [batch][n_in], y / target [batch][n_out] and grads [n_params] are device memory; every call runs
+ * on the stream given at creation (loss is returned on the host and synchronises). */
+typedef struct lb_mlp lb_mlp;
+lb_status lb_mlp_create(int n_in, int width, int n_out, int max_batch, uint64_t seed, void *cuda_stream,
+                        lb_mlp **out);
+void lb_mlp_destroy(lb_mlp *m);
+long long lb_mlp_num_params(const lb_mlp *m);
+lb_status lb_mlp_forward(lb_mlp *m, const float *x, int batch, float *y);
+lb_status lb_mlp_gradients(lb_mlp *m, const float *x, const float *target, int batch, float *grads, double *loss);
+lb_status lb_mlp_train_step(lb_mlp *m, const float *x, const float *target, int batch, float lr, double *loss);
+lb_status lb_mlp_get_params(lb_mlp *m, float *host);        /* FP32 masters -> host [n_params]     */
+lb_status lb_mlp_set_params(lb_mlp *m, const float *host);  /* host [n_params] -> masters and BF16 */
 
 long lb_step_count(const lb_handle *h);     /* steps taken since creation (or restored)      */
 int lb_uses_row_march(const lb_handle *h);  /* 1 if plain steps run on the row-march kernel   */

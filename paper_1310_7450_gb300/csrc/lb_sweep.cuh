@@ -6,11 +6,13 @@
 // by itself: per step every CTA pulls its rows (and a two-row halo, whose moments it recomputes) from
 // the channel's current population buffer in L2 (ld.global.cg: other CTAs wrote them), collides its
 // own rows into the other buffer, and the cluster meets at a hardware cluster barrier (release /
-// acquire) before the next step.  Every `check` steps the residual ||u(t)-u(t-1)||/||u(t)|| is
-// reduced across the cluster through distributed shared memory; when it is <= tol (or the channel
-// became unstable, or max_steps is reached) the whole cluster leaves and its SMs take the next
-// channel.  Channels are launched widest first.  Step counts stay multiples of `check` (even), so
-// every channel ends on the buffer it started from.
+// acquire) before the next step.  Every `check` = k steps the mean one-step change over the interval,
+// ||u(t) - u(t-k)|| / (k ||u(t)||), is reduced across the cluster through distributed shared memory
+// (over one step it would sit on the FP32 rounding floor of a steady state; over k steps that floor
+// falls as 1/k while a smooth exponential approach gives the one-step value); when it is <= tol (or
+// the channel became unstable, or max_steps is reached) the whole cluster leaves and its SMs take
+// the next channel.  Channels are launched widest first.  Step counts stay multiples of `check`
+// (even), so every channel ends on the buffer it started from.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -93,8 +95,9 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs<T, C> a) {
     for (; s < a.max_steps; ++s) {
         const T* pin = bufs[s & 1];
         T* pout = bufs[(s & 1) ^ 1];
-        const long long phase = (s + 1) % a.check;   // 0: residual step, check-1: save step
-        const bool resid = (phase == 0), save = (phase == a.check - 1) || resid;
+        // residual steps: every `check` steps; the first one only saves the velocity
+        const bool save = ((s + 1) % a.check) == 0;
+        const bool resid = save && (s + 1 >= 2 * (long long)a.check);
 
         // phase 1: own nodes (kept in registers) and halo rows -> gradient velocity in shared memory
         C d[NPT][9], dR[NPT], jx[NPT], jy[NPT];
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs<T, C> a) {
                     du2 += pq[0];
                     u2 += pq[1];
                 }
-                const double r = u2 > 0.0 ? sqrt(du2 / u2) : 0.0;
+                const double r = u2 > 0.0 ? sqrt(du2 / u2) / a.check : 0.0;
                 const bool unstable = *(volatile int*)(a.status + ch) != 0;
                 int dec = 0;
                 if (unstable) dec = 2;

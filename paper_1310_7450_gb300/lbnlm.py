@@ -76,6 +76,14 @@ def load():
         "lb_set_state": ([_H, c_void_p, c_size_t], c_int),
         "lb_channel_status": ([_H, POINTER(c_int)], c_int),
         "lb_step_count": ([_H], c_long),
+        "lb_mlp_create": ([c_int, c_int, c_int, c_int, c_uint64, c_void_p, POINTER(c_void_p)], c_int),
+        "lb_mlp_destroy": ([_H], None),
+        "lb_mlp_num_params": ([_H], ctypes.c_longlong),
+        "lb_mlp_forward": ([_H, c_void_p, c_int, c_void_p], c_int),
+        "lb_mlp_gradients": ([_H, c_void_p, c_void_p, c_int, c_void_p, POINTER(c_double)], c_int),
+        "lb_mlp_train_step": ([_H, c_void_p, c_void_p, c_int, ctypes.c_float, POINTER(c_double)], c_int),
+        "lb_mlp_get_params": ([_H, c_void_p], c_int),
+        "lb_mlp_set_params": ([_H, c_void_p], c_int),
         "lb_run_until_steady": ([_H, c_double, c_long, c_long, c_void_p, c_void_p], c_int),
         "lb_sweep_config": ([_H, POINTER(c_int), POINTER(c_int), POINTER(c_double)], c_int),
         "lb_sweep_tune": ([_H], c_int),
@@ -217,6 +225,49 @@ def lb_sweep_config(h: int):
     nt, cl, ms = c_int(), c_int(), c_double()
     _check(load().lb_sweep_config(h, ctypes.byref(nt), ctypes.byref(cl), ctypes.byref(ms)), "lb_sweep_config")
     return nt.value, cl.value, ms.value
+
+
+def lb_mlp_create(n_in: int, width: int, n_out: int, max_batch: int, seed: int = 0, stream=None) -> int:
+    m = c_void_p()
+    _check(load().lb_mlp_create(int(n_in), int(width), int(n_out), int(max_batch), int(seed), c_void_p(stream or 0),
+                                ctypes.byref(m)), "lb_mlp_create")
+    return m.value
+
+
+def lb_mlp_destroy(m: int):
+    load().lb_mlp_destroy(m)
+
+
+def lb_mlp_num_params(m: int) -> int:
+    return int(load().lb_mlp_num_params(m))
+
+
+def lb_mlp_forward(m: int, x, batch: int, y):
+    _check(load().lb_mlp_forward(m, _ptr(x), int(batch), _ptr(y)), "lb_mlp_forward")
+
+
+def lb_mlp_gradients(m: int, x, target, batch: int, grads=None) -> float:
+    loss = c_double()
+    _check(load().lb_mlp_gradients(m, _ptr(x), _ptr(target), int(batch), _ptr(grads), ctypes.byref(loss)),
+           "lb_mlp_gradients")
+    return loss.value
+
+
+def lb_mlp_train_step(m: int, x, target, batch: int, lr: float, want_loss: bool = True):
+    loss = c_double()
+    _check(load().lb_mlp_train_step(m, _ptr(x), _ptr(target), int(batch), ctypes.c_float(lr),
+                                    ctypes.byref(loss) if want_loss else None), "lb_mlp_train_step")
+    return loss.value if want_loss else None
+
+
+def lb_mlp_get_params(m: int, host: np.ndarray):
+    assert host.dtype == np.float32
+    _check(load().lb_mlp_get_params(m, c_void_p(host.ctypes.data)), "lb_mlp_get_params")
+
+
+def lb_mlp_set_params(m: int, host: np.ndarray):
+    assert host.dtype == np.float32 and host.flags["C_CONTIGUOUS"]
+    _check(load().lb_mlp_set_params(m, c_void_p(host.ctypes.data)), "lb_mlp_set_params")
 
 
 def lb_step_count(h: int) -> int:
