@@ -303,6 +303,72 @@ def run_gpu(args):
     return 0
 
 
+def run_cessation(args):
+    """Start-up then cessation of the single large channel (the throughput workload's parameters):
+    `startup` steps with the body force on, the force switched off for every later step
+    (lb_set_body_force, stream-ordered), then steps in chunks of `check` with the channel monitor
+    (max |u|, flux) between chunks until max |u| < `stop_u` (the stopping time), `max_steps` or
+    `seconds` of wall time.  Reports the stopping step if reached, the decay record and GLUPS over
+    the whole device-timed run (monitor calls included)."""
+    import torch
+    from paper_1310_7450_gb300 import build as libbuild
+    from paper_1310_7450_gb300 import lbnlm
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    libbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    cfg, p = workload(args)
+    nx, ny = cfg["nx"], cfg["ny"]
+    flags = lbnlm.LB_GRID_STORE_SIGMA if args.store_sigma else 0
+    sim = lbnlm.Channels(nx, ny, p, args.precision, stress_mode=args.stress_mode, flags=flags,
+                         stream=stream.cuda_stream)
+    mon = np.zeros(4)
+    record = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    t_wall = time.perf_counter()
+    with sampler:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        done = 0
+        while done < args.startup:
+            n = min(args.check, args.startup - done)
+            sim.step(n)
+            done += n
+            lbnlm.lb_monitor(sim.h, mon)
+            record.append((done, float(mon[2]), float(mon[1])))
+        u_startup = float(mon[2])
+        lbnlm.lb_set_body_force(sim.h, -1, 0.0)
+        stop = None
+        while done < args.startup + args.max_steps and time.perf_counter() - t_wall < args.seconds:
+            st = sim.step(args.check)
+            done += args.check
+            lbnlm.lb_monitor(sim.h, mon)
+            record.append((done, float(mon[2]), float(mon[1])))
+            if st != lbnlm.LB_OK:
+                print(json.dumps({"error": f"lb_step status {st}: {lbnlm.lb_last_error()}"}), flush=True)
+                return 1
+            if mon[2] < args.stop_u:
+                stop = done - args.startup
+                break
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    sim.close()
+    keep = sorted(set(np.unique(np.geomspace(1, len(record), 40).astype(int) - 1)))
+    line = {"metric": "start-up + cessation: GLUPS and stopping time", "value": nx * ny * done / (ms * 1e-3) / 1e9,
+            "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"single large channel {nx}x{ny}, start-up {args.startup} steps then cessation "
+                                   f"until max|u| < {args.stop_u:g}", "check_every": args.check,
+                       "store_sigma": bool(args.store_sigma)},
+            "steps_total": done, "device_ms": ms, "max_u_after_startup": u_startup,
+            "stopping_steps": stop, "stopped": stop is not None,
+            "record_step_maxu_flux": [record[i] for i in keep], "clocks": sampler.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_sweep(args):
     """Batched sweep: the 512-channel draw (Nx = 4, Ny ~ U{32..1024}, g = b (32/Ny)^2 with
     b ~ logU[1e-8, 1e-5], theta = 10^(2 + 10 eps), eps ~ U[-0.1, 0.1], seed 3), FP32, all channels
@@ -430,14 +496,19 @@ def run_warmstart(args):
         st, r, wall, fl = steady(nys, ps, start)
         res[name] = {"wall_s": wall, "converged": int((st > 0).sum()), "steps_sum": int(st[st > 0].sum()),
                      "steps_max": int(st.max()), "steps_median": float(np.median(st[st > 0])) if (st > 0).any() else None}
-        if name == "mlp":
+        if name == "analytic":
             fl_ref = fl
-    # surrogate error against the converged LB profiles (relative infinity norm per field)
-    errs = {"u": [], "sxy": [], "N1": []}
-    for k, (ny, prof) in enumerate(zip(nys, rows)):
-        u_lb = fl_ref[k][0][:, 0, 0]; s_lb = fl_ref[k][1][:, 0, 3]; n_lb = fl_ref[k][1][:, 0, 0] - fl_ref[k][1][:, 0, 1]
-        for key, a, b in (("u", prof[0], u_lb), ("sxy", prof[1], s_lb), ("N1", prof[2], n_lb)):
-            errs[key].append(float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)))
+    # error of each start against the converged LB profiles (relative infinity norm per field); the
+    # reference is the converged state of the closed-form-started run
+    def start_errors(starts):
+        errs = {"u": [], "sxy": [], "N1": []}
+        for k, prof in enumerate(starts):
+            u_lb = fl_ref[k][0][:, 0, 0]; s_lb = fl_ref[k][1][:, 0, 3]; n_lb = fl_ref[k][1][:, 0, 0] - fl_ref[k][1][:, 0, 1]
+            for key, a, b in (("u", prof[0], u_lb), ("sxy", prof[1], s_lb), ("N1", prof[2], n_lb)):
+                errs[key].append(float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)))
+        return errs
+    err_mlp = start_errors(rows)
+    err_cf = start_errors([warmstart.analytic_rows(ny, q) for ny, q in zip(nys, ps)])
     sur.close()
     line = {"metric": "batched-sweep time-to-steady, plain vs warm-start", "unit": "s", "higher_is_better": False,
             "value": res["mlp"]["wall_s"], "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
@@ -445,8 +516,10 @@ def run_warmstart(args):
                        "tol": args.tol, "check_every": args.check, "epochs": args.epochs},
             "train_data_sweep_s": wall_t, "train_s": train_s, "final_loss": losses[-1], "inference_s": infer_s,
             "held_out": res,
-            "surrogate_error_median": {k: float(np.median(v)) for k, v in errs.items()},
-            "surrogate_error_p90": {k: float(np.percentile(v, 90)) for k, v in errs.items()},
+            "start_error_median": {"mlp": {k: float(np.median(v)) for k, v in err_mlp.items()},
+                                   "closed_form": {k: float(np.median(v)) for k, v in err_cf.items()}},
+            "start_error_p90": {"mlp": {k: float(np.percentile(v, 90)) for k, v in err_mlp.items()},
+                                "closed_form": {k: float(np.percentile(v, 90)) for k, v in err_cf.items()}},
             "total_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
     return 0
@@ -468,7 +541,7 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-crop", type=int, default=256)
-    ap.add_argument("--workload", default="channel", choices=["channel", "sweep", "warmstart"])
+    ap.add_argument("--workload", default="channel", choices=["channel", "sweep", "warmstart", "cessation"])
     ap.add_argument("--train", type=int, default=20000)
     ap.add_argument("--train-seed", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=200)
@@ -481,9 +554,14 @@ def main():
     ap.add_argument("--max-steps", type=int, default=20_000_000)
     ap.add_argument("--baseline-sample", type=int, default=8)
     ap.add_argument("--baseline-steps", type=int, default=2000)
+    ap.add_argument("--startup", type=int, default=50000)
+    ap.add_argument("--stop-u", type=float, default=1e-10)
+    ap.add_argument("--seconds", type=float, default=240.0)
     args = ap.parse_args()
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "cessation":
+        return run_cessation(args)
     if args.workload == "warmstart":
         if args.sweep_seed == 3:
             args.sweep_seed = 55

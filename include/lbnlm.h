@@ -52,8 +52,9 @@ enum { LB_PREC_F64 = 0, LB_PREC_F32 = 1, LB_PREC_BF16 = 2, LB_PREC_F64S_F32M = 3
 enum { LB_STRESS_INLM = 0, LB_STRESS_TIMESTEPPED = 1 };
 /* lb_grid.flags: LB_GRID_STORE_SIGMA writes the 4-component stress every step; LB_GRID_TILE_ONLY
  * keeps every step on the general tile kernel (single wide FP32/BF16 channels otherwise use the
- * row-march kernel for the steps that need no residual or field output). */
-enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2 };
+ * row-march kernel); LB_GRID_BF16_STOCHASTIC rounds BF16 populations stochastically (unbiased:
+ * increments below half a BF16 step survive on average) instead of to nearest. */
+enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2, LB_GRID_BF16_STOCHASTIC = 4 };
 
 typedef struct {
     int n_channels;   /* >= 1                                                              */

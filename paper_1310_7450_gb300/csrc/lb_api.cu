@@ -516,6 +516,14 @@ lb_status ensure_hstage(lb_handle* h, size_t bytes) {
     return LB_OK;
 }
 
+// Key of the stochastic rounding for one step (SplitMix64 finaliser of the handle seed and step).
+uint32_t step_key(const lb_handle* h, long long step) {
+    uint64_t z = h->params[0].seed + 0x632BE59BD9B4E019ull + (uint64_t)step * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (uint32_t)(z ^ (z >> 31));
+}
+
 template <typename T, typename C>
 StepArgs<T, C> base_args(lb_handle* h) {
     StepArgs<T, C> a{};
@@ -565,6 +573,8 @@ lb_status run_steps(lb_handle* h, long n) {
         StepArgs<T, C> a = base_args<T, C>(h);
         int f = 0;
         if (h->flags & LB_GRID_STORE_SIGMA) f |= F_STORE_SIGMA;
+        if ((h->flags & LB_GRID_BF16_STOCHASTIC) && h->prec == LB_PREC_BF16) f |= F_SR;
+        a.sr_key = step_key(h, h->step);
         const bool resid = (s == n) && (h->uprev_state == h->step - 1);
         if (s >= n - 1) f |= F_SAVE_U;
         if (resid) f |= F_RESID;
@@ -650,6 +660,8 @@ cudaError_t sweep_launch(lb_handle* h, int nt, int cl, int n_clusters, double to
     a.check = check;
     a.max_steps = max_steps;
     a.tol = tol;
+    a.sr = (h->flags & LB_GRID_BF16_STOCHASTIC) && h->prec == LB_PREC_BF16;
+    a.sr_key = step_key(h, h->step + 0x5bd1e995ll);
     const size_t smem = sweep_smem(h, cl);
     if (nt == 128) return launch_sweep<T, C, 128, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
     return launch_sweep<T, C, 256, kSweepNPT>(a, n_clusters, cl, smem, h->stream);

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbk {
 
 // D2Q9 velocity set (Sec. II A).  Numbering: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1)
@@ -50,6 +52,49 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Stochastic rounding of an FP32 value to BF16: add 16 uniformly random bits below the BF16
+// mantissa and truncate, which rounds the magnitude up with probability equal to the discarded
+// fraction, so the expected stored value is v (unbiased; round-to-nearest would drop every increment
+// smaller than half a BF16 step).  Inf/NaN go through the ordinary conversion.
+__device__ __forceinline__ __nv_bfloat16 bf16_stochastic(float v, uint32_t r16) {
+    uint32_t b = __float_as_uint(v);
+    if ((b & 0x7f800000u) == 0x7f800000u) return __float2bfloat16_rn(v);
+    b += (r16 & 0xffffu);
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
+}
+
+// 32-bit integer mixer ("lowbias32" of C. Wellons' hash-prospector, public domain) used as a
+// counter-based generator: mix32(key ^ counter).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Store the nine post-collision deviations d + D of one node (node = its index in the channel
+// planes).  BF16 storage with stochastic rounding draws 16 random bits per value from
+// mix32(key ^ (5 node + pair)); `key` changes every step.
+template <typename T, typename C>
+__device__ __forceinline__ void store_node(T* po, long long P, const C (&d)[9], const C (&D)[9], bool sr, uint32_t key,
+                                           uint32_t node) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        if (sr) {
+            uint32_t h = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if ((i & 1) == 0) h = mix32(key ^ (node * 5u + (uint32_t)(i >> 1)));
+                po[(long long)i * P] = bf16_stochastic((float)(d[i] + D[i]), (i & 1) ? (h >> 16) : (h & 0xffffu));
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::st(po + (long long)i * P, d[i] + D[i]);
+}
+
 // ---- launch descriptors ----------------------------------------------------------------------
 // Per-channel constants, precomputed on the host in the arithmetic type C.
 template <typename C>
@@ -83,6 +128,7 @@ enum : int {
     F_STORE_SIGMA = 2,  // write sigma (xx, yy, zz, xy) planes this step
     F_SAVE_U = 4,       // write the reported velocity into the u_prev planes
     F_RESID = 8,        // accumulate the residual against u_prev (block partials)
+    F_SR = 16,          // BF16 storage: stochastic rounding of the populations
 };
 
 template <typename T, typename C>
@@ -103,6 +149,7 @@ struct StepArgs {
     int nx;
     int flags;
     C guard;                       // |u| above which a channel is declared unstable
+    uint32_t sr_key;               // per-step key of the stochastic rounding (F_SR)
 };
 
 // ---- per-node arithmetic -------------------------------------------------------------------

@@ -307,8 +307,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                 C D[9];
                 collide_node<C>(P, s, dcur, D);
                 T* po = a.pout + 9 * P.base + pn;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) Store<T>::st(po + i * P.P, dcur[i] + D[i]);
+                store_node<T, C>(po, P.P, dcur, D, (a.flags & F_SR) != 0, a.sr_key, (uint32_t)pn);
                 a.drho[P.base + pn] = s.drho;
                 if (SMODE == 1) {
                     C* s3 = a.sig3 + 3 * P.base;

@@ -164,8 +164,7 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
             C D[9];
             collide_node<C>(P, s, d, D);
             T* po = a.pout + 9 * P.base + pn;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) Store<T>::st(po + i * P.P, d[i] + D[i]);
+            store_node<T, C>(po, P.P, d, D, (a.flags & F_SR) != 0, a.sr_key ^ (uint32_t)(it.ch * 0x9E3779B9u), (uint32_t)pn);
             dr[pn] = s.drho;
             if (SMODE == 1) {
                 C* s3 = a.sig3 + 3 * P.base;

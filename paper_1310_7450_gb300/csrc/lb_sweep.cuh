@@ -38,6 +38,8 @@ struct SweepArgs {
     int check;                     // residual interval (even, >= 2)
     long long max_steps;           // multiple of check
     double tol;
+    bool sr;                       // BF16 storage: stochastic rounding
+    uint32_t sr_key;
 };
 
 template <typename T>
@@ -160,8 +162,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs<T, C> a) {
                 if (!velocity_ok<C>(jx[k], jy[k], rho_h, (C)0.3)) atomicOr(a.status + ch, 1);
                 C D[9];
                 collide_node<C>(P, st, d[k], D);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) Store<T>::st(pout + (long long)i * P.P + pn, d[k][i] + D[i]);
+                store_node<T, C>(pout + pn, P.P, d[k], D, a.sr, mix32(a.sr_key ^ (uint32_t)(s * 0x9E3779B9ull) ^ (uint32_t)(ch * 0x85EBCA6Bu)), (uint32_t)pn);
                 dr[pn] = st.drho;
                 if (save) {
                     const C ih = Arith<C>::div(C(1), rho_h);

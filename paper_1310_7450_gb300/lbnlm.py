@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbnlm.so
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = range(7)
 LB_PREC_F64, LB_PREC_F32, LB_PREC_BF16 = 0, 1, 2
 LB_STRESS_INLM, LB_STRESS_TIMESTEPPED = 0, 1
-LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY = 1, 2
+LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY, LB_GRID_BF16_STOCHASTIC = 1, 2, 4
 LB_PREC_F64S_F32M, LB_PREC_F32S_F64M = 3, 4
 PRECISIONS = {"f64": LB_PREC_F64, "f32": LB_PREC_F32, "bf16": LB_PREC_BF16, "f64s_f32m": LB_PREC_F64S_F32M,
               "f32s_f64m": LB_PREC_F32S_F64M}

@@ -7,9 +7,10 @@ lattice-Boltzmann scheme then relaxes to its own steady state (it stays the judg
 
 Encoding (host-side marshalling only):
   features  log10 Ny, log10 g, log10 G_inf, log10 theta, standardised with the training statistics;
-  targets   each profile divided by its maximum |value| (256 points each, d = (y - y_c)/H from -1 to 1
-            at the cell centres of 256 equal cells), plus log10 of the three maxima relative to the
-            scales u_s = g H^2 / (2 nu_LB), s_s = g H, n_s = s_s^2 / G_inf: 3 x 256 + 3 outputs.
+  targets   the steady LB profiles minus the closed-form steady profile (the discretisation error
+            of the lattice, which the network learns), each divided by the maximum |value| of the
+            closed-form field, on 256 points (d = (y - y_c)/H at the centres of 256 equal cells):
+            3 x 256 outputs.  Prediction = closed form + scale x network output.
 """
 from __future__ import annotations
 
@@ -50,16 +51,21 @@ def to_rows(profile_grid: np.ndarray, ny: int) -> np.ndarray:
     return np.interp(rows_d(ny), D_GRID, profile_grid)
 
 
+def closed_form_grid(ny: int, p: dict):
+    """Closed-form (u, sxy, N1) of the channel on the 256-point grid and the per-field scales."""
+    prof = [to_grid(f, ny) for f in analytic_rows(ny, p)]
+    sc = [max(np.abs(f).max(), 1e-300) for f in prof]
+    return prof, sc
+
+
 def encode_targets(nys, params, u_rows, sxy_rows, n1_rows) -> np.ndarray:
-    """Per channel: [u/u_max (256), sxy/|sxy|_max (256), N1/|N1|_max (256), log10 maxima / scales (3)]."""
-    out = np.zeros((len(nys), 3 * NPTS + 3))
+    """Per channel: [(LB - closed form)/scale for u, sxy, N1 on the 256 points]."""
+    out = np.zeros((len(nys), 3 * NPTS))
     for k, (ny, p) in enumerate(zip(nys, params)):
-        us, ss, ns = scales(ny, p)
-        prof = [to_grid(u_rows[k], ny), to_grid(sxy_rows[k], ny), to_grid(n1_rows[k], ny)]
-        for j, (f, s) in enumerate(zip(prof, (us, ss, ns))):
-            m = max(np.abs(f).max(), 1e-300)
-            out[k, j * NPTS:(j + 1) * NPTS] = f / m
-            out[k, 3 * NPTS + j] = math.log10(m / s)
+        ref, sc = closed_form_grid(ny, p)
+        lb = [to_grid(u_rows[k], ny), to_grid(sxy_rows[k], ny), to_grid(n1_rows[k], ny)]
+        for j in range(3):
+            out[k, j * NPTS:(j + 1) * NPTS] = (lb[j] - ref[j]) / sc[j]
     return out
 
 
@@ -67,11 +73,8 @@ def decode(nys, params, pred: np.ndarray):
     """Inverse of encode_targets on the 256-point grid: lists of (u, sxy, N1) arrays per channel."""
     res = []
     for k, (ny, p) in enumerate(zip(nys, params)):
-        us, ss, ns = scales(ny, p)
-        prof = []
-        for j, s in enumerate((us, ss, ns)):
-            prof.append(pred[k, j * NPTS:(j + 1) * NPTS] * s * 10.0 ** pred[k, 3 * NPTS + j])
-        res.append(tuple(prof))
+        ref, sc = closed_form_grid(ny, p)
+        res.append(tuple(ref[j] + sc[j] * pred[k, j * NPTS:(j + 1) * NPTS] for j in range(3)))
     return res
 
 
@@ -79,7 +82,7 @@ class Surrogate:
     """Feature / target standardisation around an lb_mlp handle."""
 
     def __init__(self, width=256, max_batch=512, seed=0, stream=None):
-        self.n_in, self.n_out, self.width = 4, 3 * NPTS + 3, width
+        self.n_in, self.n_out, self.width = 4, 3 * NPTS, width
         self.m = lbnlm.lb_mlp_create(self.n_in, width, self.n_out, max_batch, seed, stream)
         self.max_batch = max_batch
         self.fmu = self.fsd = self.tmu = self.tsd = None

@@ -378,3 +378,25 @@ def test_row_march_residual_matches_numpy(stream):
     assert mon[1] == pytest.approx(u49[..., 0].sum() / nx, rel=1e-5)
     assert mon[2] == pytest.approx(np.sqrt((u49 ** 2).sum(axis=-1)).max(), rel=1e-5)
     assert mon[3] == 49
+
+
+def test_bf16_stochastic_rounding_lets_startup_develop(stream):
+    """BF16 deviations with round-to-nearest drop per-step increments (~1e-7) that lie below half a
+    BF16 step on deviations of ~1e-3, so the start-up of the 4 x 64 theta = 100 channel stagnates;
+    stochastic rounding keeps the increments on average."""
+    cfg = inputs.oracle_channel_yield()
+    p, nx, ny, steps = cfg["params"], cfg["nx"], cfg["ny"], cfg["steps"]
+    errs = {}
+    for flags in (0, lbnlm.LB_GRID_BF16_STOCHASTIC):
+        with lbnlm.Channels(nx, ny, dict(p, seed=17), "bf16", flags=flags, stream=stream) as sim:
+            sim.step(steps)
+            (u_g, _, _), = sim.fields()
+        errs[flags] = u_g
+    st = oracle.init_state(np.ones((ny, nx)))
+    oracle.run(p, st, steps)
+    u_o, _, _ = oracle.fields(p, st)
+    e_rn = rel(errs[0], u_o)
+    e_sr = rel(errs[lbnlm.LB_GRID_BF16_STOCHASTIC], u_o)
+    print(f"BF16 start-up error: round-to-nearest {e_rn:.3e}, stochastic {e_sr:.3e}")
+    assert e_rn > 0.3
+    assert e_sr < 0.1 and e_sr < 0.2 * e_rn

@@ -31,9 +31,14 @@ def test_encode_decode_roundtrip():
     ss = [rng.uniform(-1, 1, n) for n in nys]
     ns = [rng.uniform(0, 1, n) for n in nys]
     Y = warmstart.encode_targets(nys, ps, us, ss, ns)
+    assert Y.shape == (3, 3 * warmstart.NPTS)
     back = warmstart.decode(nys, ps, Y)
     for k, ny in enumerate(nys):
         for j, src in enumerate((us, ss, ns)):
-            np.testing.assert_allclose(back[k][j], warmstart.to_grid(src[k], ny), rtol=1e-12, atol=1e-300)
+            np.testing.assert_allclose(back[k][j], warmstart.to_grid(src[k], ny), rtol=1e-10, atol=1e-12 * np.abs(src[k]).max())
+    # a zero prediction is the closed-form start
+    zero = warmstart.decode(nys, ps, np.zeros_like(Y))
+    for k, ny in enumerate(nys):
+        np.testing.assert_allclose(zero[k][0], warmstart.to_grid(warmstart.analytic_rows(ny, ps[k])[0], ny), rtol=1e-12)
     X = warmstart.features(nys, ps)
     assert X.shape == (3, 4) and np.all(np.isfinite(X))
