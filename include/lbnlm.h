@@ -53,8 +53,11 @@ enum { LB_STRESS_INLM = 0, LB_STRESS_TIMESTEPPED = 1 };
 /* lb_grid.flags: LB_GRID_STORE_SIGMA writes the 4-component stress every step; LB_GRID_TILE_ONLY
  * keeps every step on the general tile kernel (single wide FP32/BF16 channels otherwise use the
  * row-march kernel); LB_GRID_BF16_STOCHASTIC rounds BF16 populations stochastically (unbiased:
- * increments below half a BF16 step survive on average) instead of to nearest. */
-enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2, LB_GRID_BF16_STOCHASTIC = 4 };
+ * increments below half a BF16 step survive on average) instead of to nearest;
+ * LB_GRID_NO_GRAPH launches every tile-kernel step separately (by default lb_step replays runs of
+ * plain tile-kernel steps from a captured CUDA graph: the same kernels with the same arguments,
+ * bitwise the same result, without the per-launch host overhead). */
+enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2, LB_GRID_BF16_STOCHASTIC = 4, LB_GRID_NO_GRAPH = 8 };
 
 typedef struct {
     int n_channels;   /* >= 1                                                              */
@@ -205,6 +208,7 @@ lb_status lb_mlp_set_params(lb_mlp *m, const float *host);  /* host [n_params] -
 
 long lb_step_count(const lb_handle *h);     /* steps taken since creation (or restored)      */
 int lb_uses_row_march(const lb_handle *h);  /* 1 if plain steps run on the row-march kernel   */
+long lb_graph_replays(const lb_handle *h);  /* CUDA-graph launches made by lb_step so far      */
 size_t lb_num_nodes(const lb_handle *h);     /* total fluid nodes over all channels           */
 void lb_destroy(lb_handle *h);               /* synchronises the stream, frees everything     */
 const char *lb_strerror(lb_status s);

@@ -308,6 +308,12 @@ struct lb_handle {
     MarchItem* march_items_d = nullptr;
     int* march_item_begin_d = nullptr;  // {0, n_march_items}: the residual reduction's item range
     int n_march_items = 0, march_grid = 0;
+    // CUDA graphs of kGraphSteps plain tile-kernel steps, one per input buffer (an even count of
+    // steps leaves the buffers where they were, so each graph starts from the buffer it names)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    const void* gexec_pin[2] = {nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
+    long graph_replays = 0;
 };
 
 namespace {
@@ -504,6 +510,9 @@ void release(lb_handle* h) {
     if (h->gx_h) cudaFreeHost(h->gx_h);
     if (h->status_ev) cudaEventDestroy(h->status_ev);
     if (h->gx_ev) cudaEventDestroy(h->gx_ev);
+    for (int k = 0; k < 2; ++k)
+        if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 
@@ -567,13 +576,71 @@ cudaError_t launch_march<__nv_bfloat16, float>(lb_handle* h, const StepArgs<__nv
                     : launch_step_march<__nv_bfloat16, float, 0>(m, a, ctl, h->march_grid, h->stream);
 }
 
+constexpr int kGraphSteps = 32;  // steps per captured graph (even)
+
+// Capture kGraphSteps plain steps (no velocity save, no residual, no stochastic rounding) starting
+// from the current input buffer on the handle's private capture stream.
+template <typename T, typename C>
+lb_status capture_graph(lb_handle* h, int slot) {
+    if (!h->cap_stream) LB_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (h->gexec[slot]) {
+        LB_CK(cudaGraphExecDestroy(h->gexec[slot]));
+        h->gexec[slot] = nullptr;
+        h->gexec_pin[slot] = nullptr;
+    }
+    const void* pin = h->popA;
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        h->stream = user;
+        return cuda_fail(e, "graph capture begin");
+    }
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+        StepArgs<T, C> a = base_args<T, C>(h);
+        a.flags = (h->flags & LB_GRID_STORE_SIGMA) ? F_STORE_SIGMA : 0;
+        e = launch<T, C>(h, a);
+        std::swap(h->popA, h->popB);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    h->stream = user;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[slot], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->gexec[slot] = nullptr;
+        return cuda_fail(e, "graph capture");
+    }
+    h->gexec_pin[slot] = pin;
+    return LB_OK;
+}
+
 template <typename T, typename C>
 lb_status run_steps(lb_handle* h, long n) {
-    for (long s = 1; s <= n; ++s) {
+    const bool sr = (h->flags & LB_GRID_BF16_STOCHASTIC) && h->prec == LB_PREC_BF16;
+    long s = 1;
+    // Runs of plain steps replay a captured graph; the last two steps of the call (velocity save,
+    // residual) are always launched one by one.
+    if (!h->march && !sr && !(h->flags & LB_GRID_NO_GRAPH)) {
+        while (n - s + 1 >= kGraphSteps + 2) {
+            int slot = h->gexec_pin[0] == h->popA ? 0 : (h->gexec_pin[1] == h->popA ? 1 : -1);
+            if (slot < 0) {
+                slot = h->gexec_pin[0] ? 1 : 0;
+                lb_status st = capture_graph<T, C>(h, slot);
+                if (st != LB_OK) return st;
+            }
+            LB_CK(cudaGraphLaunch(h->gexec[slot], h->stream));
+            ++h->graph_replays;
+            h->step += kGraphSteps;
+            s += kGraphSteps;
+        }
+    }
+    for (; s <= n; ++s) {
         StepArgs<T, C> a = base_args<T, C>(h);
         int f = 0;
         if (h->flags & LB_GRID_STORE_SIGMA) f |= F_STORE_SIGMA;
-        if ((h->flags & LB_GRID_BF16_STOCHASTIC) && h->prec == LB_PREC_BF16) f |= F_SR;
+        if (sr) f |= F_SR;
         a.sr_key = step_key(h, h->step);
         const bool resid = (s == n) && (h->uprev_state == h->step - 1);
         if (s >= n - 1) f |= F_SAVE_U;
@@ -938,6 +1005,7 @@ void lb_destroy(lb_handle* h) { release(h); }
 
 long lb_step_count(const lb_handle* h) { return h ? h->step : -1; }
 int lb_uses_row_march(const lb_handle* h) { return (h && h->march) ? 1 : 0; }
+long lb_graph_replays(const lb_handle* h) { return h ? h->graph_replays : -1; }
 size_t lb_num_nodes(const lb_handle* h) { return h ? (size_t)h->nodes : 0; }
 
 lb_status lb_step(lb_handle* h, long n) {

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbnlm.so
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = range(7)
 LB_PREC_F64, LB_PREC_F32, LB_PREC_BF16 = 0, 1, 2
 LB_STRESS_INLM, LB_STRESS_TIMESTEPPED = 0, 1
-LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY, LB_GRID_BF16_STOCHASTIC = 1, 2, 4
+LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY, LB_GRID_BF16_STOCHASTIC, LB_GRID_NO_GRAPH = 1, 2, 4, 8
 LB_PREC_F64S_F32M, LB_PREC_F32S_F64M = 3, 4
 PRECISIONS = {"f64": LB_PREC_F64, "f32": LB_PREC_F32, "bf16": LB_PREC_BF16, "f64s_f32m": LB_PREC_F64S_F32M,
               "f32s_f64m": LB_PREC_F32S_F64M}
@@ -89,6 +89,7 @@ def load():
         "lb_sweep_tune": ([_H], c_int),
         "lb_field_monitor_static": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p], c_int),
         "lb_uses_row_march": ([_H], c_int),
+        "lb_graph_replays": ([_H], c_long),
         "lb_num_nodes": ([_H], c_size_t),
         "lb_destroy": ([_H], None),
         "lb_strerror": ([c_int], ctypes.c_char_p),
@@ -276,6 +277,10 @@ def lb_step_count(h: int) -> int:
 
 def lb_uses_row_march(h: int) -> bool:
     return bool(load().lb_uses_row_march(h))
+
+
+def lb_graph_replays(h: int) -> int:
+    return int(load().lb_graph_replays(h))
 
 
 def lb_num_nodes(h: int) -> int:
