@@ -21,6 +21,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
     run / fields     pinned: Newtonian parabola and start-up series, analytic nlM channel profile
                      (Eq. maxwellpoiseuille), mass conservation, mirror symmetry, Newtonian
                      equivalence of the forcing (below Eq. bodyforce), brute-force twin
+    GPBC runs        pinned: brute-force twin (push form), Newtonian parabola and linear pressure,
+                     continuity of the mass flux, equality with the body-force run (Sec. II B)
 """
 from __future__ import annotations
 
@@ -50,7 +52,8 @@ def build(force: bool = False) -> str:
 class OrcParams(ctypes.Structure):
     _fields_ = [("tau_lb", ctypes.c_double), ("g_x", ctypes.c_double), ("G_inf", ctypes.c_double),
                 ("tau0", ctypes.c_double), ("theta", ctypes.c_double), ("gamma_c", ctypes.c_double),
-                ("rho0", ctypes.c_double), ("stress_mode", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("rho0", ctypes.c_double), ("stress_mode", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -92,13 +95,25 @@ def _vec(x, n):
     return a
 
 
-def to_params(p) -> OrcParams:
-    """Accepts a mapping (or object) with tau_lb, g_x, G_inf, tau0, theta, gamma_c, rho0,
-    stress_mode."""
+def gpbc_densities(p, nx: int):
+    """Inlet / outlet lattice densities c_s^-2 p_+- of a pressure-driven channel (Sec. II B).
+    Reading: the imposed pressure gradient equals the body force g_x it replaces, with p_+ and p_-
+    held at the ghost columns x = -1 and x = nx, so p_+ - p_- = g_x (nx + 1), centred on rho0."""
     get = (lambda k, d=None: p.get(k, d)) if isinstance(p, dict) else (lambda k, d=None: getattr(p, k, d))
+    rho0, g = float(get("rho0", 1.0)), float(get("g_x", 0.0))
+    half = 0.5 * g * (nx + 1) * 3.0
+    return rho0 + half, rho0 - half
+
+
+def to_params(p, nx: int | None = None) -> OrcParams:
+    """Accepts a mapping (or object) with tau_lb, g_x, G_inf, tau0, theta, gamma_c, rho0,
+    stress_mode and optionally x_mode ("periodic" or "gpbc"; GPBC needs nx)."""
+    get = (lambda k, d=None: p.get(k, d)) if isinstance(p, dict) else (lambda k, d=None: getattr(p, k, d))
+    gpbc = get("x_mode", "periodic") == "gpbc"
+    rin, rout = gpbc_densities(p, nx) if gpbc else (0.0, 0.0)
     return OrcParams(float(get("tau_lb")), float(get("g_x", 0.0)), float(get("G_inf", 0.0)),
                      float(get("tau0", 0.0)), float(get("theta", 0.0)), float(get("gamma_c", np.inf)),
-                     float(get("rho0", 1.0)), int(get("stress_mode", 0)), 0)
+                     float(get("rho0", 1.0)), int(get("stress_mode", 0)), 1 if gpbc else 0, rin, rout)
 
 
 # --- per-node functions ---------------------------------------------------------------------
@@ -213,7 +228,7 @@ def flow_state(rho: np.ndarray, ux: np.ndarray, uy: np.ndarray, g_x: float) -> S
 def run(params, st: State, nsteps: int, nthreads: int = 1) -> State:
     """Advance ``st`` in place by ``nsteps`` steps; returns it."""
     ny, nx = st.shape
-    pp = to_params(params)
+    pp = to_params(params, nx)
     rc = _load().orc_run(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho), _p(st.sig),
                          int(nsteps), int(nthreads))
     if rc != 0:
@@ -229,7 +244,7 @@ def fields(params, st: State):
     u = np.zeros((ny, nx, 2))
     sg = np.zeros((ny, nx, 4))
     rho = np.zeros((ny, nx))
-    pp = to_params(params)
+    pp = to_params(params, nx)
     rc = _load().orc_fields(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho), _p(st.sig),
                             _p(u), _p(sg), _p(rho))
     if rc != 0:
@@ -241,7 +256,7 @@ def intermediates(params, st: State) -> np.ndarray:
     """[ny, nx, 8]: kxx, kxy, kyx, kyy, tau_M, drho, S, rho_eq of the next update."""
     ny, nx = st.shape
     out = np.zeros((ny, nx, 8))
-    pp = to_params(params)
+    pp = to_params(params, nx)
     rc = _load().orc_node_intermediates(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho),
                                         _p(st.sig), _p(out))
     if rc != 0:

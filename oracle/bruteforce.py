@@ -8,7 +8,10 @@ where a different but equivalent route exists:
   * tensors are full 2x2 arrays; the polymer stress solves the linear steady-state equation
     behind Eq. (sigtsum), sigma/tau_M - kappa sigma - sigma kappa^T = G D, as a 4x4 Kronecker
     system with numpy.linalg.solve (no series, no symmetric reduction);
-  * n^eq and F_i are evaluated with einsum over the velocity tensors Q_i.
+  * n^eq and F_i are evaluated with einsum over the velocity tensors Q_i;
+  * pressure-driven channels (x_mode "gpbc", Sec. II B): a population pushed across x = -1/2 or
+    x = nx - 1/2 arrives at the other end rebuilt from the node it leaves, with that node's
+    density shifted to p_+- / c_s^2 plus its deviation from its column's mean.
 Same readings of the paper as the C oracle (listed in its header).
 """
 from __future__ import annotations
@@ -31,18 +34,35 @@ def _opposite(i):
 OPP = [_opposite(i) for i in range(9)]
 
 
-def _stream_push(nstar):
+def _neq(rho, u):
+    cu = C @ u
+    return W * rho * (1 + cu / CS2 + np.einsum("iab,a,b->i", Q, u, u) / (2 * CS2 ** 2))
+
+
+def _stream_push(nstar, gpbc=None):
+    """gpbc = (rho_plus, rho_minus) for generalized periodic boundaries, None for periodic x."""
     _, ny, nx = nstar.shape
     n = np.zeros_like(nstar)
+    if gpbc is not None:
+        rho_node = nstar.sum(axis=0)
+        j_node = np.einsum("ia,iyx->yxa", C.astype(np.float64), nstar)
+        col_mean = rho_node.mean(axis=0)  # [nx]
     for i in range(9):
         for y in range(ny):
             for x in range(nx):
                 yd = y + C[i, 1]
-                xd = (x + C[i, 0]) % nx
-                if 0 <= yd < ny:
-                    n[i, yd, xd] += nstar[i, y, x]
-                else:
-                    n[OPP[i], y, x] += nstar[i, y, x]
+                xd = x + C[i, 0]
+                v = nstar[i, y, x]
+                if not 0 <= yd < ny:
+                    n[OPP[i], y, x] += v
+                    continue
+                if gpbc is not None and not 0 <= xd < nx:
+                    # leaves through the outlet (xd = nx) -> enters at the inlet with p_+, and vice versa
+                    target = gpbc[0] if xd >= nx else gpbc[1]
+                    r, jv = rho_node[y, x], j_node[y, x]
+                    r_new = target + r - col_mean[x]
+                    v = _neq(r_new, jv / r_new)[i] + (v - _neq(r, jv / r)[i])
+                n[i, yd, xd % nx] += v
     return n
 
 
@@ -69,9 +89,15 @@ def _sigma_kron(kap, tau_M, G):
 
 def step(p, nstar, drho):
     """One step; returns (new nstar, new drho, fields dict of this update)."""
-    n = _stream_push(nstar)
-    _, ny, nx = n.shape
-    f = np.array([p["g_x"], 0.0])
+    _, ny, nx = nstar.shape
+    gp = p.get("x_mode", "periodic") == "gpbc"
+    if gp:
+        dp = 1.5 * p["g_x"] * (nx + 1)          # c_s^-2 (p_+ - p_-)/2 with p_+ - p_- = g (nx + 1)
+        rho0 = p.get("rho0", 1.0)
+        n = _stream_push(nstar, (rho0 + dp, rho0 - dp))
+    else:
+        n = _stream_push(nstar)
+    f = np.array([0.0 if gp else p["g_x"], 0.0])
     R0 = n.sum(axis=0)
     j = np.einsum("ia,iyx->yxa", C.astype(np.float64), n) + 0.5 * f
     ug = j / R0[..., None]
@@ -94,13 +120,12 @@ def step(p, nstar, drho):
             tm = 0.0 if tau == 0 else 1.0 / (1.0 / tau + (0.0 if np.isinf(gc) else np.sqrt(II) / gc))
             sig = _sigma_kron(K, tm, p["G_inf"])
             snn = sig + (eta_inf - eta_N) * D
-            dr = -np.trace(snn) / (CS2 * 2)
-            S = dr - drho[y, x]
+            dr = 0.0 if gp else -np.trace(snn) / (CS2 * 2)
+            S = 0.0 if gp else dr - drho[y, x]
             sbar = snn - 0.5 * np.trace(snn) * np.eye(2)
             rho = R0[y, x] + 0.5 * S
             u = j[y, x] / rho
-            cu = C @ u
-            neq = W * rho * (1 + cu / CS2 + np.einsum("iab,a,b->i", Q, u, u) / (2 * CS2 ** 2))
+            neq = _neq(rho, u)
             Y = -S * np.outer(u, u) + np.outer(f, u) + np.outer(u, f)
             F = W * (-np.einsum("iab,ab->i", Q, sbar) / (2 * CS2 ** 2 * t)
                      + (1 - 1 / (2 * t)) * (S + (C @ f) / CS2 + np.einsum("iab,ab->i", Q, Y) / (2 * CS2 ** 2)))

@@ -39,6 +39,18 @@
  *     one-sided second-order (-3u0+4u1-u2)/2 at the first and last fluid rows;
  *   - f^ex = (g_x, 0) is a constant force density (Sec. III B: pressure drop per length);
  *   - the coefficient of the n >= 2 terms of Sigma^nN is 1, as in Eq. (sigtsum).
+ *
+ * Pressure-driven channels (boundary = 1): the generalized periodic boundaries of Sec. II B
+ * (Kim and Pitsch) replace the periodic wrap of the populations that cross x = -1/2 or
+ * x = nx - 1/2; there is no body force and no flow-induced density (delta rho = 0, so
+ * S = 0 and Eq. (bodyforce) keeps its first line only, as Sec. II B prescribes).  Readings:
+ *   - the moments (rho_s, j_s) of the node a crossing population leaves are those of its
+ *     post-collision populations (the shortened forcing has no zeroth or first moment, so the
+ *     collision keeps sum n* = R0 and sum c n* = j);
+ *   - the averaged lattice density of a boundary column is the plain mean over its rows of
+ *     sum_i n*_i;
+ *   - bounce-back takes precedence for populations whose source lies beyond a wall;
+ *   - the velocity gradients use the periodic image of the velocity field along x.
  */
 #include <math.h>
 #include <stdint.h>
@@ -67,8 +79,13 @@ typedef struct {
     double gamma_c; /* critical strain of Eq. (nlmaxwell); +inf switches thinning off */
     double rho0;    /* reference density in eta^N = rho0 c_s^2 (tau_LB - 1/2)       */
     int stress_mode;/* 0: instantaneous nlM (Eq. sigtsum); 1: backward Euler of Eq. (gkder) */
-    int pad_;
+    int boundary;   /* 0: periodic x, body force g_x; 1: generalized periodic boundaries (GPBC) */
+    double rho_in;  /* GPBC: c_s^-2 p_+, the lattice density imposed at the inlet (x = -1)    */
+    double rho_out; /* GPBC: c_s^-2 p_-, the lattice density imposed at the outlet (x = nx)   */
 } orc_params;
+
+/* the body-force density of Eq. (rhoj) / Eq. (bodyforce): none in a pressure-driven channel */
+static double body_force(const orc_params *p) { return p->boundary == 1 ? 0.0 : p->g_x; }
 
 /* ---------------------------------------------------------------------------------- */
 /* Small 2x2 tensor helpers (plain, row-major t[a][b]).                                */
@@ -382,10 +399,52 @@ static void node_update(const orc_params *p, int nx, int ny, int x, int y,
     r->sbar[2] = nn_yy - trace / ORC_DIM;
     r->drho = -trace / (ORC_CS2 * ORC_DIM);   /* flow-induced density change (Sec. II A) */
     r->S = r->drho - drho_prev[k];            /* dt d_t delta rho, Eq. (rhoplus)         */
+    if (p->boundary == 1) r->drho = r->S = 0.0; /* GPBC: no density correction (Sec. II B) */
     /* reading: sum_i n^eq = sum_i (n* + n)/2 = R0 + S/2, so that sum_i (Delta_i + F_i) = S */
     r->rho_eq_m1 = r->R0m1 + 0.5 * r->S;
     r->u[0] = r->j[0] / (1.0 + r->rho_eq_m1);
     r->u[1] = r->j[1] / (1.0 + r->rho_eq_m1);
+}
+
+/* Generalized periodic boundaries (Sec. II B): per boundary column (0: x = 0, 1: x = nx-1) the
+ * density and momentum of every node's post-collision populations and the column mean of the
+ * density.  colrho/coljx/coljy: [2][ny]; colmean: [2]. */
+static void gpbc_columns(int nx, int ny, const double *dnstar, double *colrho, double *coljx,
+                         double *coljy, double *colmean) {
+    long N = (long)nx * ny;
+    for (int c = 0; c < 2; ++c) {
+        int x = c == 0 ? 0 : nx - 1;
+        double sum = 0.0;
+        for (int y = 0; y < ny; ++y) {
+            double r = 1.0, jx = 0.0, jy = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                double v = dnstar[i * N + idx(nx, x, y)];
+                r += v;
+                jx += ORC_CX[i] * v;
+                jy += ORC_CY[i] * v;
+            }
+            colrho[c * ny + y] = r;
+            coljx[c * ny + y] = jx;
+            coljy[c * ny + y] = jy;
+            sum += r;
+        }
+        colmean[c] = sum / ny;
+    }
+}
+
+/* The population i that enters through the inlet (entering_inlet = 1: it would wrap from the
+ * outlet column) or through the outlet (0: from the inlet column) at row ys of the source node:
+ * n^eq_i(rho_target + rho_s - mean, j_s) + [n*_i(s) - n^eq_i(rho_s, j_s)], as an offset. */
+static double gpbc_ghost(const orc_params *p, int i, int entering_inlet, int ny, int ys, double dnstar_s,
+                         const double *colrho, const double *coljx, const double *coljy,
+                         const double *colmean) {
+    int c = entering_inlet ? 1 : 0; /* the column the population leaves */
+    double rho_s = colrho[c * ny + ys], jx = coljx[c * ny + ys], jy = coljy[c * ny + ys];
+    double rho_t = (entering_inlet ? p->rho_in : p->rho_out) + rho_s - colmean[c];
+    double eq_t[9], eq_s[9];
+    orc_equilibrium_offset(rho_t - 1.0, jx / rho_t, jy / rho_t, eq_t);
+    orc_equilibrium_offset(rho_s - 1.0, jx / rho_s, jy / rho_s, eq_s);
+    return eq_t[i] + (dnstar_s - eq_s[i]);
 }
 
 /* Streaming (pull form of Eq. lbupdate) plus bounce-back, then the moments of Eq. (rhoj).
@@ -393,6 +452,14 @@ static void node_update(const orc_params *p, int nx, int ny, int x, int y,
 static void stream_and_moments(const orc_params *p, int nx, int ny, const double *dnstar, double *dn,
                                double *R0m1, double *j, double *ug) {
     long N = (long)nx * ny;
+    double *colrho = NULL, *coljx = NULL, *coljy = NULL, colmean[2] = {0.0, 0.0};
+    if (p->boundary == 1) {
+        colrho = (double *)malloc(sizeof(double) * 6 * ny);
+        coljx = colrho + 2 * ny;
+        coljy = colrho + 4 * ny;
+        gpbc_columns(nx, ny, dnstar, colrho, coljx, coljy, colmean);
+    }
+    const double fx = body_force(p);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
 #endif
@@ -401,7 +468,8 @@ static void stream_and_moments(const orc_params *p, int nx, int ny, const double
             long k = idx(nx, x, y);
             double r0 = 0.0, jx = 0.0, jy = 0.0;
             for (int i = 0; i < 9; ++i) {
-                int xs = ((x - ORC_CX[i]) % nx + nx) % nx;
+                int xr = x - ORC_CX[i]; /* source column before any wrap */
+                int xs = (xr % nx + nx) % nx;
                 int ys = y - ORC_CY[i];
                 double v;
                 if (ys < 0 || ys >= ny) {
@@ -411,6 +479,9 @@ static void stream_and_moments(const orc_params *p, int nx, int ny, const double
                     for (int o = 0; o < 9; ++o)
                         if (ORC_CX[o] == -ORC_CX[i] && ORC_CY[o] == -ORC_CY[i]) opp = o;
                     v = dnstar[opp * N + k];
+                } else if (p->boundary == 1 && (xr < 0 || xr >= nx)) {
+                    v = gpbc_ghost(p, i, xr < 0, ny, ys, dnstar[i * N + idx(nx, xs, ys)], colrho, coljx,
+                                   coljy, colmean);
                 } else {
                     v = dnstar[i * N + idx(nx, xs, ys)];
                 }
@@ -420,11 +491,12 @@ static void stream_and_moments(const orc_params *p, int nx, int ny, const double
                 jy += ORC_CY[i] * v;
             }
             R0m1[k] = r0;
-            j[2 * k] = jx + 0.5 * p->g_x; /* j = sum c n + f dt/2 (Eq. rhoj, with the forcing) */
+            j[2 * k] = jx + 0.5 * fx; /* j = sum c n + f dt/2 (Eq. rhoj, with the forcing) */
             j[2 * k + 1] = jy;
             ug[2 * k] = j[2 * k] / (1.0 + r0);    /* reading: gradients from j / R0 */
             ug[2 * k + 1] = j[2 * k + 1] / (1.0 + r0);
         }
+    free(colrho);
 }
 
 typedef struct {
@@ -467,7 +539,7 @@ int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, 
                 node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
                 double dneq[9], F[9];
                 orc_equilibrium_offset(r.rho_eq_m1, r.u[0], r.u[1], dneq);
-                double f[2] = {p->g_x, 0.0};
+                double f[2] = {body_force(p), 0.0};
                 orc_forcing(p->tau_lb, r.sbar, r.S, r.u, f, F);
                 for (int i = 0; i < 9; ++i) {
                     /* BGK: n* = n - (n - n^eq)/tau_LB + F, on offsets from w_i */

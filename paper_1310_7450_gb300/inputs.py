@@ -44,6 +44,20 @@ def initial_density(nx: int, ny: int, rho0: float, amp: float, seed: int, node_o
     return (rho0 * (1.0 + amp * uniform_pm1(seed, k))).reshape(ny, nx)
 
 
+def linear_density(nx: int, ny: int, rho_in: float, rho_out: float, rho0: float = 1.0, amp: float = 0.0,
+                   seed: int = 0) -> np.ndarray:
+    """Start of a pressure-driven channel: the straight line between the densities held at the ghost
+    columns x = -1 (rho_in) and x = nx (rho_out), plus rho0 * amp * U(-1,1) at the counters of
+    ``initial_density``."""
+    x = np.arange(nx, dtype=np.float64)
+    lin = rho_in + (rho_out - rho_in) * (x + 1.0) / (nx + 1.0)
+    rho = np.repeat(lin[None, :], ny, axis=0)
+    if amp != 0.0:
+        k = np.arange(nx * ny, dtype=np.uint64) + np.uint64(1)
+        rho = rho + (rho0 * (amp * uniform_pm1(seed, k))).reshape(ny, nx)
+    return rho
+
+
 # --------------------------------------------------------------------------------------------
 # Parameter recipes.  Lattice units dx = dt = 1, c_s^2 = 1/3.  The Newtonian viscosity carried
 # by the BGK collision, eta^N = rho0 (tau_LB - 1/2)/3, is matched to the low-shear viscosity of
