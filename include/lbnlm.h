@@ -90,9 +90,23 @@ typedef struct {
     uint64_t seed;       /* SplitMix64 seed; counter = y*nx + x + 1 within the channel       */
 } lb_params;
 
+/* lb_boundary.x_mode: how the channel ends are joined.
+ *   LB_X_PERIODIC  periodic x; the flow is driven by the body force g_x (Eq. bodyforce with the
+ *                  flow-induced density of Eq. rhoplus).
+ *   LB_X_GPBC      generalized periodic boundaries (Sec. II B, after Kim and Pitsch): a population
+ *                  that crosses an end is rebuilt from the node it leaves, n^eq(rho_+- + rho_s -
+ *                  mean, j_s) + n^neq*, with rho_+- = c_s^-2 p_+- the inlet/outlet densities held at
+ *                  the ghost columns x = -1 and x = nx.  g_x is then the imposed pressure gradient:
+ *                  p_+ - p_- = g_x (nx + 1), rho_+- = rho0 +- (3/2) g_x (nx + 1); there is no body
+ *                  force and no flow-induced density (delta rho = 0, Eq. bodyforce keeps its first
+ *                  line), and lb_create starts from the linear density between rho_+ and rho_- .
+ *                  lb_set_body_force changes the pressure gradient.  Steps run on the general tile
+ *                  kernel; lb_run_until_steady / lb_sweep_tune return LB_EINVAL. */
+enum { LB_X_PERIODIC = 1, LB_X_GPBC = 2 };
+
 typedef struct {
     int walls;      /* must be 1: half-way bounce-back at both channel walls (Sec. II B)    */
-    int periodic_x; /* must be 1: periodic along the channel                                */
+    int x_mode;     /* LB_X_PERIODIC or LB_X_GPBC                                            */
 } lb_boundary;
 
 /* Create the channels on the current CUDA device, allocate their state and initialise it to

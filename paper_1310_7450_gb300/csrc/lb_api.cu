@@ -94,22 +94,30 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t counter) 
 
 struct InitChan {
     long long base, P;
-    int ny, pad_;
+    int ny, gpbc;
     double rho0, amp;
     uint64_t seed;
+    double rho_in, rho_out;  // GPBC: densities at the ghost columns x = -1 and x = nx
 };
 
-// Rest equilibrium n_i = w_i rho(r), rho = rho0 (1 + amp U(-1,1)); delta rho = 0.
+// Rest equilibrium n_i = w_i rho(r), rho = rho0 (1 + amp U(-1,1)); delta rho = 0.  Under GPBC the
+// density starts on the straight line between the inlet and outlet ghost densities (the linear
+// pre-initialisation of Sec. II B): rho = rho_in + (rho_out - rho_in)(x+1)/(nx+1) + rho0 amp U.
 template <typename T, typename C>
 __global__ void k_init(T* pop, C* drho, C* sig3, const InitChan* ch, int nx, int smode) {
     const InitChan c = ch[blockIdx.y];
     const long long n = (long long)nx * c.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         double rho = c.rho0;
+        double U = 0.0;
         if (c.amp != 0.0) {
             const uint64_t z = splitmix64(c.seed, (uint64_t)k + 1ull);
-            const double U = __dadd_rn(__dmul_rn((double)(z >> 11), 0x1p-52), -1.0);
+            U = __dadd_rn(__dmul_rn((double)(z >> 11), 0x1p-52), -1.0);
             rho = __dmul_rn(c.rho0, __dadd_rn(1.0, __dmul_rn(c.amp, U)));
+        }
+        if (c.gpbc) {
+            const double lin = c.rho_in + (c.rho_out - c.rho_in) * (double)(k % nx + 1) / (double)(nx + 1);
+            rho = __dadd_rn(lin, __dmul_rn(c.rho0, __dmul_rn(c.amp, U)));
         }
         const double dev = rho - 1.0;
 #pragma unroll
@@ -163,13 +171,14 @@ __global__ void k_planes_to_f64(const C* src, double* dst, int kp, const long lo
 template <typename T, typename C>
 __global__ void k_set_fields(T* pop, C* drho, C* sig3, const double* u, const double* rho, const double* dr,
                              const long long* base, const long long* P, const long long* node_off, const int* ny,
-                             const double* gx, int nx, int smode) {
+                             const double* gx, int nx, int smode, int gpbc) {
     const int c = blockIdx.y;
+    const double g = gpbc ? 0.0 : gx[c];  // no body force in a pressure-driven channel
     const long long n = (long long)nx * ny[c];
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const long long node = node_off[c] + k;
         const double r = rho[node];
-        const double ux = u[2 * node] - 0.5 * gx[c] / r, uy = u[2 * node + 1];
+        const double ux = u[2 * node] - 0.5 * g / r, uy = u[2 * node + 1];
         const double usq = ux * ux + uy * uy;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -178,7 +187,7 @@ __global__ void k_set_fields(T* pop, C* drho, C* sig3, const double* u, const do
             const double dev = w * ((r - 1.0) + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
             Store<T>::st(pop + 9 * base[c] + i * P[c] + k, (C)dev);
         }
-        drho[base[c] + k] = dr ? (C)dr[node] : C(0);
+        drho[base[c] + k] = (dr && !gpbc) ? (C)dr[node] : C(0);
         if (smode == 1)
             for (int j = 0; j < 3; ++j) sig3[3 * base[c] + j * P[c] + k] = C(0);
     }
@@ -186,9 +195,16 @@ __global__ void k_set_fields(T* pop, C* drho, C* sig3, const double* u, const do
 
 // Apply the per-channel body forces staged in gx (device, copied from pinned host memory).
 template <typename C>
-__global__ void k_apply_gx(ChanParams<C>* chan, const double* gx, int n_ch) {
+__global__ void k_apply_gx(ChanParams<C>* chan, const double* gx, int n_ch, int nx) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n_ch) chan[c].gx = (C)gx[c];
+    if (c >= n_ch) return;
+    if (chan[c].gpbc) {  // pressure-driven: g sets the ghost densities, there is no body force
+        const double half = 1.5 * gx[c] * (double)(nx + 1);
+        chan[c].rho_in = (C)((double)chan[c].rho_ref + half);
+        chan[c].rho_out = (C)((double)chan[c].rho_ref - half);
+    } else {
+        chan[c].gx = (C)gx[c];
+    }
 }
 
 // Per-channel reduction of the step's block partials, in a fixed order (deterministic).
@@ -314,6 +330,11 @@ struct lb_handle {
     const void* gexec_pin[2] = {nullptr, nullptr};
     cudaStream_t cap_stream = nullptr;
     long graph_replays = 0;
+    // generalized periodic boundaries (x_mode LB_X_GPBC)
+    bool gpbc = false;
+    void* gcol = nullptr;  // boundary-column moments and means (see StepArgs::gcol)
+    int gny = 0;           // sum of ny over the channels
+    std::vector<int> row_off;
 };
 
 namespace {
@@ -336,6 +357,18 @@ std::vector<ChanParams<C>> make_chan(const lb_handle* h) {
         q.tau = (C)(p.theta * p.tau0);
         q.inv_gc = std::isinf(p.gamma_c) ? C(0) : (C)(1.0 / p.gamma_c);
         q.cD = (C)(p.G_inf * p.tau0 - p.rho0 * (p.tau_lb - 0.5) / 3.0);
+        q.kdr = C(1);
+        q.rho_ref = (C)p.rho0;
+        if (h->gpbc) {
+            // GPBC (Sec. II B): the pressure gradient replaces the body force, p_+ - p_- = g (nx+1)
+            // between the ghost columns; no flow-induced density, Eq. (bodyforce) first line only
+            q.gpbc = 1;
+            q.row_off = h->row_off[c];
+            q.kdr = C(0);
+            q.gx = C(0);
+            q.rho_in = (C)(p.rho0 + 1.5 * p.g_x * (double)(h->nx + 1));
+            q.rho_out = (C)(p.rho0 - 1.5 * p.g_x * (double)(h->nx + 1));
+        }
         v[c] = q;
     }
     return v;
@@ -418,7 +451,7 @@ bool make_pop_map(const lb_handle* h, void* base, CUtensorMap* map) {
 // work items fill one wave of resident CTAs.
 lb_status plan_march(lb_handle* h) {
     h->march = false;
-    if (h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
+    if (h->gpbc || h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
         h->ny[0] < 16 || (h->flags & LB_GRID_TILE_ONLY))
         return LB_OK;
     if (!make_pop_map(h, h->popA, &h->mapA) || !make_pop_map(h, h->popB, &h->mapB)) return LB_OK;
@@ -469,8 +502,8 @@ lb_status validate(const lb_grid* g, const lb_params* p, const lb_boundary* b) {
     if (g->n_channels < 1 || g->nx < 1 || !g->ny) return fail(LB_EINVAL, "lb_create: need n_channels >= 1, nx >= 1, ny%s");
     if (g->precision < 0 || g->precision > 4) return fail(LB_EINVAL, "lb_create: unknown precision%s");
     if (g->stress_mode < 0 || g->stress_mode > 1) return fail(LB_EINVAL, "lb_create: unknown stress_mode%s");
-    if (b->walls != 1 || b->periodic_x != 1)
-        return fail(LB_EINVAL, "lb_create: only bounce-back walls with periodic x are supported%s");
+    if (b->walls != 1 || (b->x_mode != LB_X_PERIODIC && b->x_mode != LB_X_GPBC))
+        return fail(LB_EINVAL, "lb_create: need bounce-back walls and x_mode LB_X_PERIODIC or LB_X_GPBC%s");
     for (int c = 0; c < g->n_channels; ++c) {
         if (g->ny[c] < 3) return fail(LB_EINVAL, "lb_create: ny must be >= 3%s");
         if ((long long)g->ny[c] * g->nx > (1ll << 40)) return fail(LB_EINVAL, "lb_create: channel too large%s");
@@ -506,6 +539,7 @@ void release(lb_handle* h) {
     free_dev(h->sweep_steps_d);
     free_dev(h->sweep_res_d);
     free_dev(h->sweep_order_d);
+    free_dev(h->gcol);
     if (h->status_h) cudaFreeHost(h->status_h);
     if (h->gx_h) cudaFreeHost(h->gx_h);
     if (h->status_ev) cudaEventDestroy(h->status_ev);
@@ -548,7 +582,17 @@ StepArgs<T, C> base_args(lb_handle* h) {
     a.status = h->status_d;
     a.nx = h->nx;
     a.guard = (C)kGuard;
+    a.gcol = (const C*)h->gcol;
+    a.gny = h->gny;
     return a;
+}
+
+// Under GPBC every step kernel needs the boundary columns of its input buffer.
+template <typename T, typename C>
+cudaError_t gpbc_columns(lb_handle* h) {
+    if (!h->gpbc) return cudaSuccess;
+    return launch_gpbc_columns<T, C>((const T*)h->popA, (const ChanParams<C>*)h->chan, (C*)h->gcol, h->n_ch, h->nx,
+                                     h->gny, h->stream);
 }
 
 template <typename T, typename C>
@@ -599,7 +643,8 @@ lb_status capture_graph(lb_handle* h, int slot) {
     for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
         StepArgs<T, C> a = base_args<T, C>(h);
         a.flags = (h->flags & LB_GRID_STORE_SIGMA) ? F_STORE_SIGMA : 0;
-        e = launch<T, C>(h, a);
+        e = gpbc_columns<T, C>(h);
+        if (e == cudaSuccess) e = launch<T, C>(h, a);
         std::swap(h->popA, h->popB);
     }
     cudaGraph_t g = nullptr;
@@ -646,8 +691,12 @@ lb_status run_steps(lb_handle* h, long n) {
         if (s >= n - 1) f |= F_SAVE_U;
         if (resid) f |= F_RESID;
         a.flags = f;
-        if (h->march) LB_CK((launch_march<T, C>(h, a)));
-        else LB_CK((launch<T, C>(h, a)));
+        if (h->march) {
+            LB_CK((launch_march<T, C>(h, a)));
+        } else {
+            LB_CK((gpbc_columns<T, C>(h)));
+            LB_CK((launch<T, C>(h, a)));
+        }
         if (resid) {
             k_reduce_residual<<<h->n_ch, kThreads, 0, h->stream>>>(h->partials, h->march ? h->march_item_begin_d : h->item_begin_d,
                                                                     h->status_d, h->mon_d, h->nx, h->step);
@@ -668,6 +717,7 @@ lb_status fields_pass(lb_handle* h, C* fu, C* fs, C* fr) {
     a.fu = fu;
     a.fsig = fs;
     a.frho = fr;
+    LB_CK((gpbc_columns<T, C>(h)));
     LB_CK((launch<T, C>(h, a)));
     return LB_OK;
 }
@@ -826,6 +876,7 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
     if (!h || check_every < 2 || (check_every & 1) || max_steps < check_every || std::isnan(tol))
         return fail(LB_EINVAL, "lb_run_until_steady: need an even check_every >= 2 and max_steps >= check_every%s");
     if (h->smode != 0) return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements stress mode 0%s");
+    if (h->gpbc) return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements periodic x only%s");
     if (h->prec == LB_PREC_F64S_F32M || h->prec == LB_PREC_F32S_F64M)
         return fail(LB_EINVAL, "lb_run_until_steady: diagnostic precision mixes are not supported%s");
     int n_active = 0;
@@ -858,6 +909,7 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
 lb_status lb_sweep_tune(lb_handle* h) {
     if (!h) return fail(LB_EINVAL, "lb_sweep_tune: null handle%s");
     if (h->smode != 0) return fail(LB_EINVAL, "lb_sweep_tune: the sweep kernel implements stress mode 0%s");
+    if (h->gpbc) return fail(LB_EINVAL, "lb_sweep_tune: the sweep kernel implements periodic x only%s");
     int n_active = 0;
     lb_status st = sweep_order(h, &n_active);
     if (st != LB_OK || n_active == 0) return st;
@@ -917,6 +969,12 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     }
     h->planes = acc;
     h->nodes = nodes;
+    h->gpbc = boundary->x_mode == LB_X_GPBC;
+    h->row_off.resize(h->n_ch);
+    for (int c = 0; c < h->n_ch; ++c) {
+        h->row_off[c] = h->gny;
+        h->gny += h->ny[c];
+    }
     plan_tiles(h);
 
     auto dmalloc = [&](void** p, size_t bytes) -> cudaError_t { return cudaMalloc(p, bytes < 16 ? 16 : bytes); };
@@ -943,6 +1001,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     LB_ALLOC(h->node_off_d, h->n_ch * sizeof(long long));
     LB_ALLOC(h->ny_d, h->n_ch * sizeof(int));
     LB_ALLOC(h->gx_d, h->n_ch * sizeof(double));
+    if (h->gpbc) LB_ALLOC(h->gcol, (6 * (size_t)h->gny + 2 * h->n_ch) * h->csize);
 #undef LB_ALLOC
     e = cudaMallocHost((void**)&h->status_h, h->n_ch * sizeof(int));
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
@@ -957,7 +1016,9 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     std::vector<InitChan> ic(h->n_ch);
     for (int c = 0; c < h->n_ch; ++c) {
         gx[c] = h->params[c].g_x;
-        ic[c] = InitChan{h->base[c], h->P[c], h->ny[c], 0, h->params[c].rho0, h->params[c].rho_pert_amp, h->params[c].seed};
+        const double half = 1.5 * h->params[c].g_x * (double)(h->nx + 1);
+        ic[c] = InitChan{h->base[c], h->P[c], h->ny[c], h->gpbc ? 1 : 0, h->params[c].rho0, h->params[c].rho_pert_amp,
+                         h->params[c].seed, h->params[c].rho0 + half, h->params[c].rho0 - half};
     }
     InitChan* ic_d = nullptr;
     e = cudaMalloc(&ic_d, sizeof(InitChan) * h->n_ch);
@@ -1081,8 +1142,8 @@ lb_status lb_set_body_force(lb_handle* h, int channel, double g_x) {
     LB_CK(cudaMemcpyAsync(h->gx_d, h->gx_h, sizeof(double) * h->n_ch, cudaMemcpyHostToDevice, h->stream));
     LB_CK(cudaEventRecord(h->gx_ev, h->stream));
     h->gx_pending = true;
-    if (h->csize == 8) k_apply_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->gx_d, h->n_ch);
-    else k_apply_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->gx_d, h->n_ch);
+    if (h->csize == 8) k_apply_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->gx_d, h->n_ch, h->nx);
+    else k_apply_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->gx_d, h->n_ch, h->nx);
     LB_CK(cudaGetLastError());
     return LB_OK;
 }
@@ -1104,7 +1165,8 @@ lb_status lb_set_fields(lb_handle* h, const double* u, const double* rho, const 
     with_types(h->prec, [&](auto tt, auto tc) {
         LB_TYPES(tt, tc);
         k_set_fields<T, C><<<g, 256, 0, h->stream>>>((T*)h->popA, (C*)h->drho, (C*)h->sig3, su, sr, drho ? sd : nullptr,
-                                                     h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode);
+                                                     h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode,
+                                                     h->gpbc ? 1 : 0);
         return 0;
     });
     LB_CK(cudaGetLastError());

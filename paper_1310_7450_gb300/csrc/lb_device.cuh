@@ -103,6 +103,8 @@ struct ChanParams {
     long long P;         // plane stride (elements), >= nx*ny, padded
     long long node_off;  // compact node offset of the channel (field outputs)
     int ny;
+    int gpbc;     // 1: generalized periodic boundaries along x (pressure-driven, Sec. II B)
+    int row_off;  // first row of the channel in the stacked boundary-column arrays (GPBC)
     int pad_;
     C omega;    // 1/tau_LB (BGK)
     C k1;       // -1/(2 c_s^4 tau_LB) = -9/(2 tau_LB): traceless-stress line of Eq. (bodyforce)
@@ -112,6 +114,10 @@ struct ChanParams {
     C tau;      // theta * tau0
     C inv_gc;   // 1/gamma_c (0 = no shear thinning)
     C cD;       // eta_inf - eta^N = G tau0 - rho0 (tau_LB - 1/2)/3: Sigma^nN = sigma + cD D
+    C kdr;      // 1 with the flow-induced density of Eq. (rhoplus); 0 under GPBC (Sec. II B)
+    C rho_ref;  // rho0
+    C rho_in;   // GPBC: c_s^-2 p_+ at the inlet ghost column x = -1
+    C rho_out;  // GPBC: c_s^-2 p_- at the outlet ghost column x = nx
 };
 
 struct WorkItem {
@@ -150,6 +156,10 @@ struct StepArgs {
     int flags;
     C guard;                       // |u| above which a channel is declared unstable
     uint32_t sr_key;               // per-step key of the stochastic rounding (F_SR)
+    const C* __restrict__ gcol;    // GPBC boundary columns of pin (null: periodic x), layout
+                                   // [comp rho, jx, jy][col 0: x = 0, 1: x = nx-1][row], then
+                                   // the column means [channel][col]
+    int gny;                       // rows of all channels (the row stride of gcol)
 };
 
 // ---- per-node arithmetic -------------------------------------------------------------------
@@ -185,6 +195,19 @@ __device__ __forceinline__ void gradient_velocity(const C (&d)[9], C gx, C& dR, 
     const C inv = Arith<C>::div(C(1), C(1) + dR);
     ux = jx * inv;
     uy = jy * inv;
+}
+
+// Generalized periodic boundaries (Sec. II B, after Kim and Pitsch): a population that crosses
+// the end of the channel is rebuilt from the node it leaves as n^eq_i(rho_s + delta, j_s) +
+// n^neq*_i, with n^neq*_i = n*_i - n^eq_i(rho_s, j_s) and delta = rho_target - (column mean).
+// With n^eq_i(rho, j) = w_i [rho + 3 c.j + (4.5 (c.j)^2 - 1.5 j^2) / rho] the rebuilt value is
+// n*_i + w_i [delta - (4.5 (c.j)^2 - 1.5 j^2) delta / (rho_s (rho_s + delta))].  rho_s and j_s
+// are the moments of the node's post-collision populations (the shortened forcing keeps both).
+template <typename C>
+__device__ __forceinline__ C gpbc_shift(int i, C rho_s, C jx, C jy, C delta) {
+    const C cj = C(cx(i)) * jx + C(cy(i)) * jy;
+    const C q = C(4.5) * cj * cj - C(1.5) * (jx * jx + jy * jy);
+    return wgt<C>(i) * (delta - q * Arith<C>::div(delta, rho_s * (rho_s + delta)));
 }
 
 // Polymer stress sigma = (xx, xy, yy) solving  s - alpha (kappa s + s kappa^T) = b  in closed
@@ -243,8 +266,8 @@ __device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C k
     const C Nxy = r.sxy + P.cD * Dxy;
     const C Nyy = r.syy + P.cD * Dyy;
     const C T = Nxx + Nyy;
-    r.drho = C(-1.5) * T;             // -tr Sigma^nN / (c_s^2 d), d = 2
-    r.S = r.drho - drho_prev;         // dt d_t delta rho (Eq. rhoplus)
+    r.drho = P.kdr * (C(-1.5) * T);   // -tr Sigma^nN / (c_s^2 d), d = 2 (none under GPBC)
+    r.S = r.drho - P.kdr * drho_prev; // dt d_t delta rho (Eq. rhoplus)
     r.Bxx = C(0.5) * (Nxx - Nyy);
     r.Bxy = Nxy;
     r.dReq = dR + C(0.5) * r.S;

@@ -16,18 +16,34 @@
 
 namespace lbk {
 
+// Boundary-column data of one channel under GPBC (col == nullptr: periodic x).
+template <typename C>
+struct GpbcView {
+    const C* col;  // gcol + row_off: rho at [c * gny + y], jx at [(2 + c) * gny + y], jy at [(4 + c) * gny + y]
+    int gny;
+    C dplus;       // rho_in - mean rho of the outlet column (populations entering at x = 0)
+    C dminus;      // rho_out - mean rho of the inlet column (populations entering at x = nx-1)
+};
+
 template <typename T, typename C>
 __device__ __forceinline__ void pull9(const T* __restrict__ pc, long long P, int nx, int ny, int x, int y,
-                                      C (&d)[9]) {
+                                      C (&d)[9], const GpbcView<C>& g) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int ys = y - cy(i);
         if (ys < 0 || ys >= ny) {
             d[i] = Store<T>::ld(pc + (long long)opp(i) * P + (long long)y * nx + x);
         } else {
-            int xs = x - cx(i);
-            xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+            const int xr = x - cx(i);
+            const int xs = xr < 0 ? xr + nx : (xr >= nx ? xr - nx : xr);
             d[i] = Store<T>::ld(pc + (long long)i * P + (long long)ys * nx + xs);
+            if (g.col && xs != xr) {
+                // crossing the end of the channel: rebuilt from the node it leaves (column
+                // c = 1 for x = nx-1 when entering the inlet, c = 0 when entering the outlet)
+                const int c = xr < 0 ? 1 : 0;
+                d[i] += gpbc_shift<C>(i, g.col[c * g.gny + ys], g.col[(2 + c) * g.gny + ys],
+                                      g.col[(4 + c) * g.gny + ys], xr < 0 ? g.dplus : g.dminus);
+            }
         }
     }
 }
@@ -62,6 +78,11 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
     const int t = threadIdx.x;
     const int ntile = it.nxt * it.nyt;
     const T* pc = a.pin + 9 * P.base;
+    GpbcView<C> gv{nullptr, 0, C(0), C(0)};
+    if (a.gcol && P.gpbc) {
+        const C* means = a.gcol + 6LL * a.gny + 2 * it.ch;
+        gv = GpbcView<C>{a.gcol + P.row_off, a.gny, P.rho_in - means[1], P.rho_out - means[0]};
+    }
 
     // phase 1: own node
     const bool own = t < ntile;
@@ -71,7 +92,7 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
     C d[9];
     C dR = C(0), jx = C(0), jy = C(0);
     if (own) {
-        pull9<T, C>(pc, P.P, nx, ny, x, y, d);
+        pull9<T, C>(pc, P.P, nx, ny, x, y, d, gv);
         C ux, uy;
         gradient_velocity<C>(d, P.gx, dR, jx, jy, ux, uy);
         const int e = (ty + 1) * EX + (tx + ex0);
@@ -91,7 +112,7 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
             int hx = full ? ex : it.x0 - 1 + ex;
             hx = hx < 0 ? hx + nx : (hx >= nx ? hx - nx : hx);
             C dh[9], hR, hjx, hjy;
-            pull9<T, C>(pc, P.P, nx, ny, hx, hy, dh);
+            pull9<T, C>(pc, P.P, nx, ny, hx, hy, dh, gv);
             gradient_velocity<C>(dh, P.gx, hR, hjx, hjy, ux, uy);
         }
         const int e = ey * EX + ex;
@@ -212,9 +233,52 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
     }
 }
 
+// GPBC boundary columns of the stored state: per node of the columns x = 0 and x = nx-1 the
+// density and momentum of its post-collision populations, and per column the mean density
+// (a fixed-order block reduction, so every step kernel sees the same value).  One CTA per
+// (channel, column); channels without GPBC are skipped.
+template <typename T, typename C, int NT>
+__global__ void __launch_bounds__(NT) k_gpbc_columns(const T* __restrict__ pin, const ChanParams<C>* __restrict__ chan,
+                                                     C* __restrict__ gcol, int nx, int gny) {
+    const int ch = blockIdx.x >> 1, c = blockIdx.x & 1;
+    const ChanParams<C> P = chan[ch];
+    if (!P.gpbc) return;
+    const int x = c ? nx - 1 : 0;
+    const T* pc = pin + 9 * P.base;
+    C* col = gcol + P.row_off;
+    double sum = 0.0;
+    for (int y = threadIdx.x; y < P.ny; y += NT) {
+        C d[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = Store<T>::ld(pc + (long long)i * P.P + (long long)y * nx + x);
+        C dR, jx, jy;
+        moments<C>(d, dR, jx, jy);
+        const C rho = C(1) + dR;
+        col[c * gny + y] = rho;
+        col[(2 + c) * gny + y] = jx;
+        col[(4 + c) * gny + y] = jy;
+        sum += (double)rho;
+    }
+    __shared__ double red[NT];
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gcol[6LL * gny + 2 * ch + c] = (C)(red[0] / (double)P.ny);
+}
+
 }  // namespace lbk
 
 namespace lbk {
+template <typename T, typename C>
+cudaError_t launch_gpbc_columns(const T* pin, const ChanParams<C>* chan, C* gcol, int n_ch, int nx, int gny,
+                                cudaStream_t s) {
+    k_gpbc_columns<T, C, 256><<<2 * n_ch, 256, 0, s>>>(pin, chan, gcol, nx, gny);
+    return cudaGetLastError();
+}
+
 // Host-side launcher, explicitly instantiated per storage type in lb_kernels_*.cu.
 template <typename T, typename C, int SMODE>
 cudaError_t launch_step_tile(const StepArgs<T, C>& a, int n_items, size_t smem, cudaStream_t s) {

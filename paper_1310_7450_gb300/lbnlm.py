@@ -22,6 +22,8 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = ra
 LB_PREC_F64, LB_PREC_F32, LB_PREC_BF16 = 0, 1, 2
 LB_STRESS_INLM, LB_STRESS_TIMESTEPPED = 0, 1
 LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY, LB_GRID_BF16_STOCHASTIC, LB_GRID_NO_GRAPH = 1, 2, 4, 8
+LB_X_PERIODIC, LB_X_GPBC = 1, 2
+X_MODES = {"periodic": LB_X_PERIODIC, "gpbc": LB_X_GPBC}
 LB_PREC_F64S_F32M, LB_PREC_F32S_F64M = 3, 4
 PRECISIONS = {"f64": LB_PREC_F64, "f32": LB_PREC_F32, "bf16": LB_PREC_BF16, "f64s_f32m": LB_PREC_F64S_F32M,
               "f32s_f64m": LB_PREC_F32S_F64M}
@@ -39,7 +41,7 @@ class lb_params(ctypes.Structure):
 
 
 class lb_boundary(ctypes.Structure):
-    _fields_ = [("walls", c_int), ("periodic_x", c_int)]
+    _fields_ = [("walls", c_int), ("x_mode", c_int)]
 
 
 class LBError(RuntimeError):
@@ -136,15 +138,16 @@ def make_params(p: dict, rho_pert_amp: float = 0.0, seed: int = 0) -> lb_params:
 # ---- the C calls ---------------------------------------------------------------------------
 
 def lb_create(nx: int, ny, params, precision: int = LB_PREC_F64, stress_mode: int = LB_STRESS_INLM,
-              flags: int = 0, stream: int | None = None) -> int:
-    """ny: int or list per channel; params: dict / lb_params or a list of them (one per channel)."""
+              flags: int = 0, stream: int | None = None, x_mode: int = LB_X_PERIODIC) -> int:
+    """ny: int or list per channel; params: dict / lb_params or a list of them (one per channel);
+    x_mode: LB_X_PERIODIC (body-force driven) or LB_X_GPBC (pressure-driven)."""
     lib = load()
     nys = [int(ny)] if np.isscalar(ny) else [int(v) for v in ny]
     plist = params if isinstance(params, (list, tuple)) else [params] * len(nys)
     arr = (lb_params * len(nys))(*[p if isinstance(p, lb_params) else make_params(p) for p in plist])
     nyarr = (c_int * len(nys))(*nys)
     grid = lb_grid(len(nys), int(nx), nyarr, int(precision), int(stress_mode), int(flags))
-    bnd = lb_boundary(1, 1)
+    bnd = lb_boundary(1, int(x_mode))
     h = c_void_p()
     _check(lib.lb_create(ctypes.byref(grid), arr, ctypes.byref(bnd), c_void_p(stream or 0), ctypes.byref(h)),
            "lb_create")
@@ -304,11 +307,12 @@ def lb_last_error() -> str:
 class Channels:
     """Owns one handle; returns fields as NumPy arrays shaped per channel."""
 
-    def __init__(self, nx, ny, params, precision="f64", stress_mode=0, flags=0, stream=None):
+    def __init__(self, nx, ny, params, precision="f64", stress_mode=0, flags=0, stream=None, x_mode="periodic"):
         self.nx = int(nx)
         self.ny = [int(ny)] if np.isscalar(ny) else [int(v) for v in ny]
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        self.h = lb_create(self.nx, self.ny, params, prec, stress_mode, flags, stream)
+        xm = X_MODES[x_mode] if isinstance(x_mode, str) else int(x_mode)
+        self.h = lb_create(self.nx, self.ny, params, prec, stress_mode, flags, stream, xm)
         self.nodes = lb_num_nodes(self.h)
 
     def close(self):

@@ -1,0 +1,152 @@
+"""GPU parity of the pressure-driven channel (generalized periodic boundaries, Sec. II B) against
+the FP64 oracle on the same inputs: FP64 within 1e-12, FP32 within 1e-5 on u and sigma; grids
+with full-width tiles (nx <= 64, x wraps inside the tile) and with split tiles whose halo columns
+cross the channel ends (nx > 64), several channels in one handle, graph replay, the pressure
+switch of lb_set_body_force and the linear start of lb_create."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_7450_gb300 import inputs, lbnlm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+def rel(a, b):
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def nlm(theta=10.0, g=1e-4, G=1e-3):
+    return inputs.matched_params(0.9, theta, 0.1, G, g)
+
+
+def gp(p):
+    return dict(p, x_mode="gpbc")
+
+
+def random_state(nx, ny, seed, amp=1e-2):
+    rng = np.random.default_rng(seed)
+    st = oracle.init_state(1.0 + amp * rng.uniform(-1, 1, (ny, nx)))
+    w = oracle.equilibrium(1.0, 0.0, 0.0)
+    st.dev += amp * rng.uniform(-1, 1, st.dev.shape) * w[:, None, None]
+    return st
+
+
+@pytest.mark.parametrize("nx,ny", [(4, 37), (1, 9), (2, 3), (40, 13), (96, 21), (129, 10)])
+def test_gpbc_fp64_random_state_matches_oracle(stream, nx, ny):
+    p = nlm()
+    st = random_state(nx, ny, 500 + nx * 3 + ny)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream, x_mode="gpbc") as sim:
+        sim.set_populations([st.nstar], [st.drho])
+        sim.step(40)
+        (n_g, d_g), = sim.populations()
+        (u_g, s_g, r_g), = sim.fields()
+    oracle.run(gp(p), st, 40)
+    u_o, s_o, r_o = oracle.fields(gp(p), st)
+    assert rel(n_g, st.nstar) < 1e-14
+    assert np.all(d_g == 0.0)
+    assert rel(u_g, u_o) < 1e-12
+    assert rel(s_g, s_o) < 1e-11
+    assert rel(r_g - 1, r_o - 1) < 1e-11
+
+
+def test_gpbc_linear_start_matches_input_generator(stream):
+    nx, ny = 70, 11
+    p = dict(nlm(), rho_pert_amp=1e-3, seed=77)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream, x_mode="gpbc") as sim:
+        (n_g, d_g), = sim.populations()
+    rin, rout = oracle.gpbc_densities(p, nx)
+    rho = inputs.linear_density(nx, ny, rin, rout, 1.0, 1e-3, 77)
+    assert np.abs(n_g.sum(axis=0) - rho).max() < 1e-15
+    assert np.all(d_g == 0)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_gpbc_yield_stress_channel_from_linear_start(stream, prec, tol):
+    """4 x 64 yield-stress channel (theta = 100, gamma_c = 0.1, wp H = 1/2) started from the
+    linear density, 20000 steps."""
+    nx, ny = 4, 64
+    p = inputs.yield_stress_channel(ny)
+    with lbnlm.Channels(nx, ny, p, prec, stream=stream, x_mode="gpbc") as sim:
+        sim.step(20000)
+        (u_g, s_g, _), = sim.fields()
+    rin, rout = oracle.gpbc_densities(p, nx)
+    st = oracle.init_state(inputs.linear_density(nx, ny, rin, rout))
+    oracle.run(gp(p), st, 20000)
+    u_o, s_o, _ = oracle.fields(gp(p), st)
+    print(f"GPBC {prec}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e}")
+    assert rel(u_g, u_o) < tol
+    assert rel(s_g, s_o) < (tol if prec == "f64" else 5e-5)
+
+
+def test_gpbc_batch_equals_solo_and_graph_equals_launches(stream):
+    nys = [17, 64, 9]
+    ps = [nlm(10.0, 1e-4), nlm(100.0, 3e-5, 2e-3), nlm(0.0, 1e-5)]
+    ps = [dict(q, rho_pert_amp=1e-3, seed=s) for q, s in zip(ps, [1, 2, 3])]
+    out = {}
+    for flags in (0, lbnlm.LB_GRID_NO_GRAPH):
+        with lbnlm.Channels(4, nys, ps, "f64", flags=flags, stream=stream, x_mode="gpbc") as sim:
+            sim.step(301)
+            out[flags] = (sim.populations(), lbnlm.lb_graph_replays(sim.h))
+    assert out[0][1] > 0 and out[lbnlm.LB_GRID_NO_GRAPH][1] == 0
+    for (a, da), (b, db) in zip(out[0][0], out[lbnlm.LB_GRID_NO_GRAPH][0]):
+        assert np.array_equal(a, b) and np.array_equal(da, db)
+    for k, (ny, q) in enumerate(zip(nys, ps)):
+        with lbnlm.Channels(4, ny, q, "f64", stream=stream, x_mode="gpbc") as solo:
+            solo.step(301)
+            (n1, d1), = solo.populations()
+        assert np.array_equal(n1, out[0][0][k][0])
+
+
+def test_gpbc_pressure_switch_off(stream):
+    """lb_set_body_force(0) under GPBC sets p_+ = p_- (cessation of the pressure-driven flow)."""
+    nx, ny = 4, 32
+    p = nlm(100.0, 2e-6)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream, x_mode="gpbc") as sim:
+        sim.step(3000)
+        lbnlm.lb_set_body_force(sim.h, -1, 0.0)
+        sim.step(2000)
+        (u_g, s_g, r_g), = sim.fields()
+    rin, rout = oracle.gpbc_densities(p, nx)
+    st = oracle.init_state(inputs.linear_density(nx, ny, rin, rout))
+    oracle.run(gp(p), st, 3000)
+    oracle.run(gp(dict(p, g_x=0.0)), st, 2000)
+    u_o, s_o, r_o = oracle.fields(gp(dict(p, g_x=0.0)), st)
+    assert rel(u_g, u_o) < 1e-12 and rel(s_g, s_o) < 1e-11 and rel(r_g - 1, r_o - 1) < 1e-11
+
+
+def test_gpbc_set_fields_matches_oracle(stream):
+    nx, ny = 4, 24
+    p = nlm(10.0, 1e-5)
+    rng = np.random.default_rng(3)
+    u = np.zeros((ny, nx, 2))
+    u[..., 0] = 1e-2 * rng.uniform(0, 1, (ny, nx))
+    rin, rout = oracle.gpbc_densities(p, nx)
+    rho = inputs.linear_density(nx, ny, rin, rout)
+    with lbnlm.Channels(nx, ny, p, "f64", stream=stream, x_mode="gpbc") as sim:
+        lbnlm.lb_set_fields(sim.h, np.ascontiguousarray(u.reshape(-1)), np.ascontiguousarray(rho.reshape(-1)), None)
+        sim.step(500)
+        (u_g, s_g, _), = sim.fields()
+    st = oracle.flow_state(rho, u[..., 0], u[..., 1], 0.0)
+    oracle.run(gp(p), st, 500)
+    u_o, s_o, _ = oracle.fields(gp(p), st)
+    assert rel(u_g, u_o) < 1e-12 and rel(s_g, s_o) < 1e-11
+
+
+def test_gpbc_rejected_by_the_sweep(stream):
+    with lbnlm.Channels(4, [16, 20], nlm(), "f32", stream=stream, x_mode="gpbc") as sim:
+        assert not lbnlm.lb_uses_row_march(sim.h)
+        with pytest.raises(lbnlm.LBError) as e:
+            sim.run_until_steady(1e-8, check_every=100, max_steps=1000)
+        assert e.value.status == lbnlm.LB_EINVAL
+    with lbnlm.Channels(4096, 64, nlm(), "f32", stream=stream, x_mode="gpbc") as wide:
+        assert not lbnlm.lb_uses_row_march(wide.h)
