@@ -23,6 +23,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                      equivalence of the forcing (below Eq. bodyforce), brute-force twin
     GPBC runs        pinned: brute-force twin (push form), Newtonian parabola and linear pressure,
                      continuity of the mass flux, equality with the body-force run (Sec. II B)
+    Couette runs     pinned: brute-force twin, exact linear Newtonian profile, start-up Fourier
+                     series, homogeneous nlM shear (Sec. III A closed forms), mass invariance
 """
 from __future__ import annotations
 
@@ -53,7 +55,8 @@ class OrcParams(ctypes.Structure):
     _fields_ = [("tau_lb", ctypes.c_double), ("g_x", ctypes.c_double), ("G_inf", ctypes.c_double),
                 ("tau0", ctypes.c_double), ("theta", ctypes.c_double), ("gamma_c", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("stress_mode", ctypes.c_int), ("boundary", ctypes.c_int),
-                ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double)]
+                ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double), ("top_wall", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("u_wall", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -107,13 +110,16 @@ def gpbc_densities(p, nx: int):
 
 def to_params(p, nx: int | None = None) -> OrcParams:
     """Accepts a mapping (or object) with tau_lb, g_x, G_inf, tau0, theta, gamma_c, rho0,
-    stress_mode and optionally x_mode ("periodic" or "gpbc"; GPBC needs nx)."""
+    stress_mode and optionally x_mode ("periodic" or "gpbc"; GPBC needs nx), top_wall
+    ("bounce_back" or "moving": planar Couette flow with a Zou-He wall on the last row) and
+    u_wall."""
     get = (lambda k, d=None: p.get(k, d)) if isinstance(p, dict) else (lambda k, d=None: getattr(p, k, d))
     gpbc = get("x_mode", "periodic") == "gpbc"
     rin, rout = gpbc_densities(p, nx) if gpbc else (0.0, 0.0)
     return OrcParams(float(get("tau_lb")), float(get("g_x", 0.0)), float(get("G_inf", 0.0)),
                      float(get("tau0", 0.0)), float(get("theta", 0.0)), float(get("gamma_c", np.inf)),
-                     float(get("rho0", 1.0)), int(get("stress_mode", 0)), 1 if gpbc else 0, rin, rout)
+                     float(get("rho0", 1.0)), int(get("stress_mode", 0)), 1 if gpbc else 0, rin, rout,
+                     1 if get("top_wall", "bounce_back") == "moving" else 0, 0, float(get("u_wall", 0.0)))
 
 
 # --- per-node functions ---------------------------------------------------------------------

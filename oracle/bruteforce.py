@@ -11,7 +11,10 @@ where a different but equivalent route exists:
   * n^eq and F_i are evaluated with einsum over the velocity tensors Q_i;
   * pressure-driven channels (x_mode "gpbc", Sec. II B): a population pushed across x = -1/2 or
     x = nx - 1/2 arrives at the other end rebuilt from the node it leaves, with that node's
-    density shifted to p_+- / c_s^2 plus its deviation from its column's mean.
+    density shifted to p_+- / c_s^2 plus its deviation from its column's mean;
+  * planar Couette flow (top_wall "moving"): after streaming, the last row's unknown populations
+    solve the four conditions of Zou and He as a linear system (density unknown, wall velocity
+    (u_wall, 0), non-equilibrium bounce-back of the wall-normal population).
 Same readings of the paper as the C oracle (listed in its header).
 """
 from __future__ import annotations
@@ -66,6 +69,30 @@ def _stream_push(nstar, gpbc=None):
     return n
 
 
+def _zou_he_top(n, u_wall):
+    """Unknowns (rho, n_4, n_7, n_8) at every node of the last row from: sum_i n_i = rho,
+    sum_i c_iy n_i = 0, sum_i c_ix n_i = rho u_wall, n_4 - n_2 = n^eq_4 - n^eq_2 (= 0 for u_y = 0)."""
+    _, ny, nx = n.shape
+    y = ny - 1
+    unk = [4, 7, 8]
+    for x in range(nx):
+        known = [i for i in range(9) if i not in unk]
+        # rows: mass, y-momentum, x-momentum, normal bounce-back; columns: rho, n4, n7, n8
+        A = np.zeros((4, 4))
+        b = np.zeros(4)
+        A[0] = [-1.0, 1.0, 1.0, 1.0]
+        b[0] = -sum(n[i, y, x] for i in known)
+        A[1] = [0.0] + [float(C[i, 1]) for i in unk]
+        b[1] = -sum(C[i, 1] * n[i, y, x] for i in known)
+        A[2] = [-u_wall] + [float(C[i, 0]) for i in unk]
+        b[2] = -sum(C[i, 0] * n[i, y, x] for i in known)
+        A[3] = [0.0, 1.0, 0.0, 0.0]
+        b[3] = n[2, y, x]
+        sol = np.linalg.solve(A, b)
+        for k, i in enumerate(unk):
+            n[i, y, x] = sol[k + 1]
+
+
 def _grad(u):
     """u[ny, nx, 2] -> kappa[ny, nx, 2, 2] with kappa[a, b] = d_b u_a (three-point stencils)."""
     ny, nx, _ = u.shape
@@ -97,6 +124,8 @@ def step(p, nstar, drho):
         n = _stream_push(nstar, (rho0 + dp, rho0 - dp))
     else:
         n = _stream_push(nstar)
+    if p.get("top_wall", "bounce_back") == "moving":
+        _zou_he_top(n, p.get("u_wall", 0.0))
     f = np.array([0.0 if gp else p["g_x"], 0.0])
     R0 = n.sum(axis=0)
     j = np.einsum("ia,iyx->yxa", C.astype(np.float64), n) + 0.5 * f

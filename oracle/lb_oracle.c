@@ -51,6 +51,14 @@
  *     sum_i n*_i;
  *   - bounce-back takes precedence for populations whose source lies beyond a wall;
  *   - the velocity gradients use the periodic image of the velocity field along x.
+ *
+ * Planar Couette flow (top_wall = 1, Sec. II B and Sec. IV C): the last fluid row y = ny-1 lies
+ * on a wall moving with (u_wall, 0); its three populations arriving from beyond the wall are
+ * set by the construction of Zou and He instead of bounce-back: the density follows from the
+ * mass and wall-normal momentum of the known populations, the normal population from the
+ * bounce-back of its non-equilibrium part, the two diagonal ones from the wall's tangential
+ * momentum.  The bottom wall stays the half-way bounce-back wall at y = -1/2, so the gap is
+ * ny - 1/2.
  */
 #include <math.h>
 #include <stdint.h>
@@ -82,6 +90,9 @@ typedef struct {
     int boundary;   /* 0: periodic x, body force g_x; 1: generalized periodic boundaries (GPBC) */
     double rho_in;  /* GPBC: c_s^-2 p_+, the lattice density imposed at the inlet (x = -1)    */
     double rho_out; /* GPBC: c_s^-2 p_-, the lattice density imposed at the outlet (x = nx)   */
+    int top_wall;   /* 0: half-way bounce-back; 1: wall on row ny-1 moving with u_wall (Zou-He) */
+    int pad_;
+    double u_wall;  /* tangential velocity of the moving wall                                   */
 } orc_params;
 
 /* the body-force density of Eq. (rhoj) / Eq. (bodyforce): none in a pressure-driven channel */
@@ -489,6 +500,24 @@ static void stream_and_moments(const orc_params *p, int nx, int ny, const double
                 r0 += v;
                 jx += ORC_CX[i] * v;
                 jy += ORC_CY[i] * v;
+            }
+            if (p->top_wall == 1 && y == ny - 1) {
+                /* Zou-He moving wall: replace the three populations that came from beyond the
+                 * wall (c_y = -1: directions 4, 7, 8).  On offsets (w_4 = w_2, w_7 = w_5, w_8 = w_6,
+                 * and the known weights w_0 + w_1 + w_3 + 2 (w_2 + w_5 + w_6) sum to 1). */
+                double *d = dn + k;
+                double known = d[0 * N] + d[1 * N] + d[3 * N] + 2.0 * (d[2 * N] + d[5 * N] + d[6 * N]);
+                double rho = 1.0 + known;          /* u_y = 0 at the wall */
+                double half_t = 0.5 * (d[1 * N] - d[3 * N]);
+                d[4 * N] = d[2 * N];
+                d[7 * N] = d[5 * N] + half_t - 0.5 * rho * p->u_wall;
+                d[8 * N] = d[6 * N] - half_t + 0.5 * rho * p->u_wall;
+                r0 = 0.0; jx = 0.0; jy = 0.0;
+                for (int i = 0; i < 9; ++i) {
+                    r0 += d[i * N];
+                    jx += ORC_CX[i] * d[i * N];
+                    jy += ORC_CY[i] * d[i * N];
+                }
             }
             R0m1[k] = r0;
             j[2 * k] = jx + 0.5 * fx; /* j = sum c n + f dt/2 (Eq. rhoj, with the forcing) */
