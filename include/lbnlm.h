@@ -103,9 +103,18 @@ typedef struct {
  *                  lb_set_body_force changes the pressure gradient.  Steps run on the general tile
  *                  kernel; lb_run_until_steady / lb_sweep_tune return LB_EINVAL. */
 enum { LB_X_PERIODIC = 1, LB_X_GPBC = 2 };
+/* lb_boundary.walls:
+ *   LB_WALLS_BOUNCE_BACK  half-way bounce-back walls at y = -1/2 and y = ny - 1/2 (Sec. II B).
+ *   LB_WALLS_COUETTE      planar Couette flow (Sec. IV C): half-way bounce-back at y = -1/2; the
+ *                         last row y = ny-1 lies on a wall moving with (u_wall, 0) whose incoming
+ *                         populations follow Zou and He (gap ny - 1/2).  u_wall starts at 0 and is
+ *                         set with lb_set_wall_velocity.  The prescribed velocity is that of the
+ *                         wall row's populations, j / sum_i n_i.  Steps run on the general tile
+ *                         kernel; lb_run_until_steady / lb_sweep_tune return LB_EINVAL. */
+enum { LB_WALLS_BOUNCE_BACK = 1, LB_WALLS_COUETTE = 2 };
 
 typedef struct {
-    int walls;      /* must be 1: half-way bounce-back at both channel walls (Sec. II B)    */
+    int walls;      /* LB_WALLS_BOUNCE_BACK or LB_WALLS_COUETTE                             */
     int x_mode;     /* LB_X_PERIODIC or LB_X_GPBC                                            */
 } lb_boundary;
 
@@ -143,6 +152,11 @@ lb_status lb_monitor(lb_handle *h, double *out);
  * ordered: the force goes host -> device from pinned memory and applies to every step enqueued
  * after this call; the call does not wait for the steps enqueued before it. */
 lb_status lb_set_body_force(lb_handle *h, int channel, double g_x);
+
+/* Set the velocity of the moving wall of one channel (channel = -1: all) of a LB_WALLS_COUETTE
+ * handle: start-up (u_wall > 0) and cessation (0) of planar Couette flow.  Stream-ordered like
+ * lb_set_body_force.  LB_EINVAL for handles without a moving wall. */
+lb_status lb_set_wall_velocity(lb_handle *h, int channel, double u_wall);
 
 /* Warm start: set every node to the equilibrium of the given hydrodynamic density and velocity
  * (host, node order: u [node][2], rho [node]), with the population current chosen so that

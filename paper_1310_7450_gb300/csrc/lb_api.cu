@@ -193,11 +193,13 @@ __global__ void k_set_fields(T* pop, C* drho, C* sig3, const double* u, const do
     }
 }
 
-// Apply the per-channel body forces staged in gx (device, copied from pinned host memory).
+// Apply the per-channel body forces (gx[0..n_ch)) and moving-wall velocities (gx[n_ch..2 n_ch))
+// staged in gx (device, copied from pinned host memory).
 template <typename C>
 __global__ void k_apply_gx(ChanParams<C>* chan, const double* gx, int n_ch, int nx) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_ch) return;
+    chan[c].u_wall = (C)gx[n_ch + c];  // staged after the forces: the moving-wall velocities
     if (chan[c].gpbc) {  // pressure-driven: g sets the ghost densities, there is no body force
         const double half = 1.5 * gx[c] * (double)(nx + 1);
         chan[c].rho_in = (C)((double)chan[c].rho_ref + half);
@@ -335,6 +337,9 @@ struct lb_handle {
     void* gcol = nullptr;  // boundary-column moments and means (see StepArgs::gcol)
     int gny = 0;           // sum of ny over the channels
     std::vector<int> row_off;
+    // planar Couette flow (walls LB_WALLS_COUETTE): Zou-He moving wall on the last row
+    bool moving = false;
+    std::vector<double> u_wall;
 };
 
 namespace {
@@ -359,6 +364,8 @@ std::vector<ChanParams<C>> make_chan(const lb_handle* h) {
         q.cD = (C)(p.G_inf * p.tau0 - p.rho0 * (p.tau_lb - 0.5) / 3.0);
         q.kdr = C(1);
         q.rho_ref = (C)p.rho0;
+        q.moving = h->moving ? 1 : 0;
+        q.u_wall = (C)h->u_wall[c];
         if (h->gpbc) {
             // GPBC (Sec. II B): the pressure gradient replaces the body force, p_+ - p_- = g (nx+1)
             // between the ghost columns; no flow-induced density, Eq. (bodyforce) first line only
@@ -451,7 +458,7 @@ bool make_pop_map(const lb_handle* h, void* base, CUtensorMap* map) {
 // work items fill one wave of resident CTAs.
 lb_status plan_march(lb_handle* h) {
     h->march = false;
-    if (h->gpbc || h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
+    if (h->gpbc || h->moving || h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
         h->ny[0] < 16 || (h->flags & LB_GRID_TILE_ONLY))
         return LB_OK;
     if (!make_pop_map(h, h->popA, &h->mapA) || !make_pop_map(h, h->popB, &h->mapB)) return LB_OK;
@@ -502,8 +509,9 @@ lb_status validate(const lb_grid* g, const lb_params* p, const lb_boundary* b) {
     if (g->n_channels < 1 || g->nx < 1 || !g->ny) return fail(LB_EINVAL, "lb_create: need n_channels >= 1, nx >= 1, ny%s");
     if (g->precision < 0 || g->precision > 4) return fail(LB_EINVAL, "lb_create: unknown precision%s");
     if (g->stress_mode < 0 || g->stress_mode > 1) return fail(LB_EINVAL, "lb_create: unknown stress_mode%s");
-    if (b->walls != 1 || (b->x_mode != LB_X_PERIODIC && b->x_mode != LB_X_GPBC))
-        return fail(LB_EINVAL, "lb_create: need bounce-back walls and x_mode LB_X_PERIODIC or LB_X_GPBC%s");
+    if ((b->walls != LB_WALLS_BOUNCE_BACK && b->walls != LB_WALLS_COUETTE) ||
+        (b->x_mode != LB_X_PERIODIC && b->x_mode != LB_X_GPBC))
+        return fail(LB_EINVAL, "lb_create: walls must be LB_WALLS_BOUNCE_BACK or LB_WALLS_COUETTE and x_mode LB_X_PERIODIC or LB_X_GPBC%s");
     for (int c = 0; c < g->n_channels; ++c) {
         if (g->ny[c] < 3) return fail(LB_EINVAL, "lb_create: ny must be >= 3%s");
         if ((long long)g->ny[c] * g->nx > (1ll << 40)) return fail(LB_EINVAL, "lb_create: channel too large%s");
@@ -585,6 +593,23 @@ StepArgs<T, C> base_args(lb_handle* h) {
     a.gcol = (const C*)h->gcol;
     a.gny = h->gny;
     return a;
+}
+
+// Body forces and wall velocities: host -> pinned staging -> device -> channel table, all
+// stream-ordered (the staging buffer is reused only after its previous copy ran).
+lb_status push_drive(lb_handle* h) {
+    if (h->gx_pending) LB_CK(cudaEventSynchronize(h->gx_ev));
+    for (int c = 0; c < h->n_ch; ++c) {
+        h->gx_h[c] = h->params[c].g_x;
+        h->gx_h[h->n_ch + c] = h->u_wall[c];
+    }
+    LB_CK(cudaMemcpyAsync(h->gx_d, h->gx_h, sizeof(double) * 2 * h->n_ch, cudaMemcpyHostToDevice, h->stream));
+    LB_CK(cudaEventRecord(h->gx_ev, h->stream));
+    h->gx_pending = true;
+    if (h->csize == 8) k_apply_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->gx_d, h->n_ch, h->nx);
+    else k_apply_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->gx_d, h->n_ch, h->nx);
+    LB_CK(cudaGetLastError());
+    return LB_OK;
 }
 
 // Under GPBC every step kernel needs the boundary columns of its input buffer.
@@ -876,7 +901,8 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
     if (!h || check_every < 2 || (check_every & 1) || max_steps < check_every || std::isnan(tol))
         return fail(LB_EINVAL, "lb_run_until_steady: need an even check_every >= 2 and max_steps >= check_every%s");
     if (h->smode != 0) return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements stress mode 0%s");
-    if (h->gpbc) return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements periodic x only%s");
+    if (h->gpbc || h->moving)
+        return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements periodic x and bounce-back walls only%s");
     if (h->prec == LB_PREC_F64S_F32M || h->prec == LB_PREC_F32S_F64M)
         return fail(LB_EINVAL, "lb_run_until_steady: diagnostic precision mixes are not supported%s");
     int n_active = 0;
@@ -909,7 +935,8 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
 lb_status lb_sweep_tune(lb_handle* h) {
     if (!h) return fail(LB_EINVAL, "lb_sweep_tune: null handle%s");
     if (h->smode != 0) return fail(LB_EINVAL, "lb_sweep_tune: the sweep kernel implements stress mode 0%s");
-    if (h->gpbc) return fail(LB_EINVAL, "lb_sweep_tune: the sweep kernel implements periodic x only%s");
+    if (h->gpbc || h->moving)
+        return fail(LB_EINVAL, "lb_sweep_tune: the sweep kernel implements periodic x and bounce-back walls only%s");
     int n_active = 0;
     lb_status st = sweep_order(h, &n_active);
     if (st != LB_OK || n_active == 0) return st;
@@ -970,6 +997,8 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     h->planes = acc;
     h->nodes = nodes;
     h->gpbc = boundary->x_mode == LB_X_GPBC;
+    h->moving = boundary->walls == LB_WALLS_COUETTE;
+    h->u_wall.assign(h->n_ch, 0.0);
     h->row_off.resize(h->n_ch);
     for (int c = 0; c < h->n_ch; ++c) {
         h->row_off[c] = h->gny;
@@ -1000,19 +1029,19 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     LB_ALLOC(h->P_d, h->n_ch * sizeof(long long));
     LB_ALLOC(h->node_off_d, h->n_ch * sizeof(long long));
     LB_ALLOC(h->ny_d, h->n_ch * sizeof(int));
-    LB_ALLOC(h->gx_d, h->n_ch * sizeof(double));
+    LB_ALLOC(h->gx_d, 2 * h->n_ch * sizeof(double));
     if (h->gpbc) LB_ALLOC(h->gcol, (6 * (size_t)h->gny + 2 * h->n_ch) * h->csize);
 #undef LB_ALLOC
     e = cudaMallocHost((void**)&h->status_h, h->n_ch * sizeof(int));
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
-    e = cudaMallocHost((void**)&h->gx_h, h->n_ch * sizeof(double));
+    e = cudaMallocHost((void**)&h->gx_h, 2 * h->n_ch * sizeof(double));
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
     e = cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gx_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaEventCreate"));
 
     // tables (synchronous copies: creation is not on the hot path)
-    std::vector<double> gx(h->n_ch);
+    std::vector<double> gx(2 * h->n_ch, 0.0);
     std::vector<InitChan> ic(h->n_ch);
     for (int c = 0; c < h->n_ch; ++c) {
         gx[c] = h->params[c].g_x;
@@ -1038,7 +1067,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     ok &= cudaMemcpy(h->P_d, h->P.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(h->node_off_d, h->node_off.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(h->ny_d, h->ny.data(), sizeof(int) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok &= cudaMemcpy(h->gx_d, gx.data(), sizeof(double) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(h->gx_d, gx.data(), sizeof(double) * 2 * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemsetAsync(h->status_d, 0, sizeof(int) * h->n_ch, h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(h->uprev, 0, 2 * h->planes * h->csize, h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(h->popB, 0, 9 * h->planes * h->tsize, h->stream) == cudaSuccess;
@@ -1136,16 +1165,16 @@ lb_status lb_set_body_force(lb_handle* h, int channel, double g_x) {
         return fail(LB_EINVAL, "lb_set_body_force: bad argument%s");
     for (int c = 0; c < h->n_ch; ++c)
         if (channel < 0 || c == channel) h->params[c].g_x = g_x;
-    // stream-ordered: the pinned staging buffer is reused only after its previous copy ran
-    if (h->gx_pending) LB_CK(cudaEventSynchronize(h->gx_ev));
-    for (int c = 0; c < h->n_ch; ++c) h->gx_h[c] = h->params[c].g_x;
-    LB_CK(cudaMemcpyAsync(h->gx_d, h->gx_h, sizeof(double) * h->n_ch, cudaMemcpyHostToDevice, h->stream));
-    LB_CK(cudaEventRecord(h->gx_ev, h->stream));
-    h->gx_pending = true;
-    if (h->csize == 8) k_apply_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->gx_d, h->n_ch, h->nx);
-    else k_apply_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->gx_d, h->n_ch, h->nx);
-    LB_CK(cudaGetLastError());
-    return LB_OK;
+    return push_drive(h);
+}
+
+lb_status lb_set_wall_velocity(lb_handle* h, int channel, double u_wall) {
+    if (!h || channel < -1 || channel >= h->n_ch || std::isnan(u_wall) || std::isinf(u_wall))
+        return fail(LB_EINVAL, "lb_set_wall_velocity: bad argument%s");
+    if (!h->moving) return fail(LB_EINVAL, "lb_set_wall_velocity: the handle has no moving wall%s");
+    for (int c = 0; c < h->n_ch; ++c)
+        if (channel < 0 || c == channel) h->u_wall[c] = u_wall;
+    return push_drive(h);
 }
 
 lb_status lb_set_fields(lb_handle* h, const double* u, const double* rho, const double* drho) {

@@ -105,7 +105,7 @@ struct ChanParams {
     int ny;
     int gpbc;     // 1: generalized periodic boundaries along x (pressure-driven, Sec. II B)
     int row_off;  // first row of the channel in the stacked boundary-column arrays (GPBC)
-    int pad_;
+    int moving;   // 1: the last row lies on a wall moving with (u_wall, 0) (Zou-He, Sec. IV C)
     C omega;    // 1/tau_LB (BGK)
     C k1;       // -1/(2 c_s^4 tau_LB) = -9/(2 tau_LB): traceless-stress line of Eq. (bodyforce)
     C k2;       // 1 - 1/(2 tau_LB)
@@ -118,6 +118,7 @@ struct ChanParams {
     C rho_ref;  // rho0
     C rho_in;   // GPBC: c_s^-2 p_+ at the inlet ghost column x = -1
     C rho_out;  // GPBC: c_s^-2 p_- at the outlet ghost column x = nx
+    C u_wall;   // tangential velocity of the moving wall (moving == 1)
 };
 
 struct WorkItem {
@@ -208,6 +209,21 @@ __device__ __forceinline__ C gpbc_shift(int i, C rho_s, C jx, C jy, C delta) {
     const C cj = C(cx(i)) * jx + C(cy(i)) * jy;
     const C q = C(4.5) * cj * cj - C(1.5) * (jx * jx + jy * jy);
     return wgt<C>(i) * (delta - q * Arith<C>::div(delta, rho_s * (rho_s + delta)));
+}
+
+// Moving wall on the last row (Zou and He): the populations arriving from beyond the wall
+// (directions 4, 7, 8) follow from the wall velocity (u_wall, 0): density from the mass and
+// wall-normal momentum of the six known populations, n_4 by bounce-back of the non-equilibrium
+// part, n_7 and n_8 from the tangential momentum rho u_wall.  On deviations the known weights sum
+// to 1 and w_4 = w_2, w_7 = w_5, w_8 = w_6.
+template <typename C>
+__device__ __forceinline__ void zou_he_top(C (&d)[9], C u_wall) {
+    const C rho = C(1) + (d[0] + d[1] + d[3] + C(2) * (d[2] + d[5] + d[6]));
+    const C ht = C(0.5) * (d[1] - d[3]);
+    const C hm = C(0.5) * rho * u_wall;
+    d[4] = d[2];
+    d[7] = d[5] + ht - hm;
+    d[8] = d[6] - ht + hm;
 }
 
 // Polymer stress sigma = (xx, xy, yy) solving  s - alpha (kappa s + s kappa^T) = b  in closed

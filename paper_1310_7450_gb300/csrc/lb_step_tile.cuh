@@ -16,13 +16,15 @@
 
 namespace lbk {
 
-// Boundary-column data of one channel under GPBC (col == nullptr: periodic x).
+// Boundary data of one channel: GPBC columns (col == nullptr: periodic x) and the moving wall.
 template <typename C>
 struct GpbcView {
     const C* col;  // gcol + row_off: rho at [c * gny + y], jx at [(2 + c) * gny + y], jy at [(4 + c) * gny + y]
     int gny;
     C dplus;       // rho_in - mean rho of the outlet column (populations entering at x = 0)
     C dminus;      // rho_out - mean rho of the inlet column (populations entering at x = nx-1)
+    int moving;    // 1: Zou-He moving wall on the last row
+    C u_wall;
 };
 
 template <typename T, typename C>
@@ -46,6 +48,7 @@ __device__ __forceinline__ void pull9(const T* __restrict__ pc, long long P, int
             }
         }
     }
+    if (g.moving && y == ny - 1) zou_he_top<C>(d, g.u_wall);
 }
 
 template <typename C>
@@ -78,10 +81,13 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
     const int t = threadIdx.x;
     const int ntile = it.nxt * it.nyt;
     const T* pc = a.pin + 9 * P.base;
-    GpbcView<C> gv{nullptr, 0, C(0), C(0)};
+    GpbcView<C> gv{nullptr, 0, C(0), C(0), P.moving, P.u_wall};
     if (a.gcol && P.gpbc) {
         const C* means = a.gcol + 6LL * a.gny + 2 * it.ch;
-        gv = GpbcView<C>{a.gcol + P.row_off, a.gny, P.rho_in - means[1], P.rho_out - means[0]};
+        gv.col = a.gcol + P.row_off;
+        gv.gny = a.gny;
+        gv.dplus = P.rho_in - means[1];
+        gv.dminus = P.rho_out - means[0];
     }
 
     // phase 1: own node

@@ -24,6 +24,8 @@ LB_STRESS_INLM, LB_STRESS_TIMESTEPPED = 0, 1
 LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY, LB_GRID_BF16_STOCHASTIC, LB_GRID_NO_GRAPH = 1, 2, 4, 8
 LB_X_PERIODIC, LB_X_GPBC = 1, 2
 X_MODES = {"periodic": LB_X_PERIODIC, "gpbc": LB_X_GPBC}
+LB_WALLS_BOUNCE_BACK, LB_WALLS_COUETTE = 1, 2
+WALLS = {"bounce_back": LB_WALLS_BOUNCE_BACK, "couette": LB_WALLS_COUETTE}
 LB_PREC_F64S_F32M, LB_PREC_F32S_F64M = 3, 4
 PRECISIONS = {"f64": LB_PREC_F64, "f32": LB_PREC_F32, "bf16": LB_PREC_BF16, "f64s_f32m": LB_PREC_F64S_F32M,
               "f32s_f64m": LB_PREC_F32S_F64M}
@@ -70,6 +72,7 @@ def load():
         "lb_residual": ([_H, _D], c_int),
         "lb_monitor": ([_H, _D], c_int),
         "lb_set_body_force": ([_H, c_int, c_double], c_int),
+        "lb_set_wall_velocity": ([_H, c_int, c_double], c_int),
         "lb_set_fields": ([_H, _D, _D, _D], c_int),
         "lb_set_populations": ([_H, _D, _D, _D], c_int),
         "lb_get_populations": ([_H, _D, _D, _D], c_int),
@@ -138,16 +141,18 @@ def make_params(p: dict, rho_pert_amp: float = 0.0, seed: int = 0) -> lb_params:
 # ---- the C calls ---------------------------------------------------------------------------
 
 def lb_create(nx: int, ny, params, precision: int = LB_PREC_F64, stress_mode: int = LB_STRESS_INLM,
-              flags: int = 0, stream: int | None = None, x_mode: int = LB_X_PERIODIC) -> int:
+              flags: int = 0, stream: int | None = None, x_mode: int = LB_X_PERIODIC,
+              walls: int = LB_WALLS_BOUNCE_BACK) -> int:
     """ny: int or list per channel; params: dict / lb_params or a list of them (one per channel);
-    x_mode: LB_X_PERIODIC (body-force driven) or LB_X_GPBC (pressure-driven)."""
+    x_mode: LB_X_PERIODIC (body-force driven) or LB_X_GPBC (pressure-driven); walls:
+    LB_WALLS_BOUNCE_BACK or LB_WALLS_COUETTE (moving top wall)."""
     lib = load()
     nys = [int(ny)] if np.isscalar(ny) else [int(v) for v in ny]
     plist = params if isinstance(params, (list, tuple)) else [params] * len(nys)
     arr = (lb_params * len(nys))(*[p if isinstance(p, lb_params) else make_params(p) for p in plist])
     nyarr = (c_int * len(nys))(*nys)
     grid = lb_grid(len(nys), int(nx), nyarr, int(precision), int(stress_mode), int(flags))
-    bnd = lb_boundary(1, int(x_mode))
+    bnd = lb_boundary(int(walls), int(x_mode))
     h = c_void_p()
     _check(lib.lb_create(ctypes.byref(grid), arr, ctypes.byref(bnd), c_void_p(stream or 0), ctypes.byref(h)),
            "lb_create")
@@ -176,6 +181,10 @@ def lb_monitor(h: int, out: np.ndarray):
 
 def lb_set_body_force(h: int, channel: int, g_x: float):
     _check(load().lb_set_body_force(h, int(channel), float(g_x)), "lb_set_body_force")
+
+
+def lb_set_wall_velocity(h: int, channel: int, u_wall: float):
+    _check(load().lb_set_wall_velocity(h, int(channel), float(u_wall)), "lb_set_wall_velocity")
 
 
 def lb_set_fields(h: int, u: np.ndarray, rho: np.ndarray, drho: np.ndarray | None = None):
@@ -307,12 +316,14 @@ def lb_last_error() -> str:
 class Channels:
     """Owns one handle; returns fields as NumPy arrays shaped per channel."""
 
-    def __init__(self, nx, ny, params, precision="f64", stress_mode=0, flags=0, stream=None, x_mode="periodic"):
+    def __init__(self, nx, ny, params, precision="f64", stress_mode=0, flags=0, stream=None, x_mode="periodic",
+                 walls="bounce_back"):
         self.nx = int(nx)
         self.ny = [int(ny)] if np.isscalar(ny) else [int(v) for v in ny]
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         xm = X_MODES[x_mode] if isinstance(x_mode, str) else int(x_mode)
-        self.h = lb_create(self.nx, self.ny, params, prec, stress_mode, flags, stream, xm)
+        wl = WALLS[walls] if isinstance(walls, str) else int(walls)
+        self.h = lb_create(self.nx, self.ny, params, prec, stress_mode, flags, stream, xm, wl)
         self.nodes = lb_num_nodes(self.h)
 
     def close(self):
