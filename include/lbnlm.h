@@ -148,6 +148,13 @@ lb_status lb_residual(lb_handle *h, double *r);
  * (residual, flux = sum over nodes of u_x / nx, max |u|, step index of the evaluated state). */
 lb_status lb_monitor(lb_handle *h, double *out);
 
+/* The same diagnostics without waiting: enqueues their copy into out ([n_channels][4], pinned
+ * host memory or device memory) on the handle's stream and returns at once.  The values are
+ * there when the stream has passed this point (cudaStreamSynchronize, or an event recorded after
+ * the call); a monitoring loop can read step k's diagnostics while step k+1 runs.  LB_ESTATE if
+ * no residual has been evaluated yet. */
+lb_status lb_monitor_async(lb_handle *h, double *out);
+
 /* Change the body force of one channel (channel = -1: all), e.g. 0 for cessation.  Stream-
  * ordered: the force goes host -> device from pinned memory and applies to every step enqueued
  * after this call; the call does not wait for the steps enqueued before it. */

@@ -1151,6 +1151,13 @@ lb_status lb_monitor(lb_handle* h, double* out) {
     return LB_OK;
 }
 
+lb_status lb_monitor_async(lb_handle* h, double* out) {
+    if (!h || !out) return fail(LB_EINVAL, "lb_monitor_async: null argument%s");
+    if (h->mon_state < 0) return fail(LB_ESTATE, "lb_monitor_async: no residual evaluated yet (run lb_step with n >= 2)%s");
+    LB_CK(cudaMemcpyAsync(out, h->mon_d, 4 * h->n_ch * sizeof(double), cudaMemcpyDefault, h->stream));
+    return LB_OK;
+}
+
 lb_status lb_residual(lb_handle* h, double* r) {
     if (!h || !r) return fail(LB_EINVAL, "lb_residual: null argument%s");
     std::vector<double> m(4 * (size_t)h->n_ch);

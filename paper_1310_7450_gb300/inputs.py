@@ -155,10 +155,10 @@ def steady_peak_speed(ny: int, g: float, G: float, tau0: float, theta: float, ga
 
 
 def sweep_channel_params(n_channels: int, seed: int, tau_lb: float = 0.9, gamma_c: float = 0.1,
-                         u_max: float = 0.05):
+                         u_max: float = 0.05, ny_lo: int = 32, ny_hi: int = 1024):
     """Parameters of the batched sweep: g = b (32/Ny)^2; G_inf the smallest value >= 1e-6 whose
     steady peak speed is <= u_max (bisection in log G)."""
-    ny, b, eps = sweep_draws(n_channels, seed)
+    ny, b, eps = sweep_draws(n_channels, seed, ny_lo, ny_hi)
     theta = theta_of_eps(eps)
     out = []
     for k in range(n_channels):

@@ -71,6 +71,7 @@ def load():
         "lb_get_fields": ([_H, c_void_p, c_void_p, c_void_p, c_int, c_int], c_int),
         "lb_residual": ([_H, _D], c_int),
         "lb_monitor": ([_H, _D], c_int),
+        "lb_monitor_async": ([_H, c_void_p], c_int),
         "lb_set_body_force": ([_H, c_int, c_double], c_int),
         "lb_set_wall_velocity": ([_H, c_int, c_double], c_int),
         "lb_set_fields": ([_H, _D, _D, _D], c_int),
@@ -177,6 +178,11 @@ def lb_residual(h: int, out: np.ndarray):
 
 def lb_monitor(h: int, out: np.ndarray):
     _check(load().lb_monitor(h, _dp(out)), "lb_monitor")
+
+
+def lb_monitor_async(h: int, out):
+    """out: a pinned host tensor / array or a device tensor of n_channels * 4 doubles."""
+    _check(load().lb_monitor_async(h, _ptr(out)), "lb_monitor_async")
 
 
 def lb_set_body_force(h: int, channel: int, g_x: float):

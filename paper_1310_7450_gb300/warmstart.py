@@ -155,6 +155,24 @@ def analytic_rows(ny: int, p: dict, n: int = 4001):
     return u, sxy, n1
 
 
+def judge(nx, nys, params, candidates, precision="f32", stream=None, check=1000):
+    """The lattice-Boltzmann scheme as the judge of the starts: every candidate (a list of per-channel
+    (u_x, sigma_xy, N1) row profiles) runs two check intervals of the batched sweep; per channel the
+    candidate with the smallest check-interval residual wins.  Returns (chosen rows, index of the
+    winning candidate per channel)."""
+    res = []
+    for rows in candidates:
+        sim = lbnlm.Channels(nx, nys, params, precision, stream=stream)
+        try:
+            apply(sim, rows)
+            _, r = sim.run_until_steady(0.0, check_every=check, max_steps=2 * check)
+        finally:
+            sim.close()
+        res.append(np.where(np.isfinite(r), r, np.inf))
+    pick = np.argmin(np.array(res), axis=0)
+    return [candidates[k][c] for c, k in enumerate(pick)], pick
+
+
 def apply(sim, rows_by_channel):
     """Write (u_x, sigma_xy, N1) row profiles into every channel of ``sim`` (an lbnlm.Channels):
     u = (u_x, 0), rho = 1 and the stored flow-induced density delta rho = -(3/2) tr sigma with
