@@ -98,14 +98,20 @@ def _vec(x, n):
     return a
 
 
-def gpbc_densities(p, nx: int):
-    """Inlet / outlet lattice densities c_s^-2 p_+- of a pressure-driven channel (Sec. II B).
+def gpbc_density_offsets(p, nx: int):
+    """Inlet / outlet lattice densities c_s^-2 p_+- of a pressure-driven channel (Sec. II B), minus 1.
     Reading: the imposed pressure gradient equals the body force g_x it replaces, with p_+ and p_-
     held at the ghost columns x = -1 and x = nx, so p_+ - p_- = g_x (nx + 1), centred on rho0."""
     get = (lambda k, d=None: p.get(k, d)) if isinstance(p, dict) else (lambda k, d=None: getattr(p, k, d))
     rho0, g = float(get("rho0", 1.0)), float(get("g_x", 0.0))
     half = 0.5 * g * (nx + 1) * 3.0
-    return rho0 + half, rho0 - half
+    return (rho0 - 1.0) + half, (rho0 - 1.0) - half
+
+
+def gpbc_densities(p, nx: int):
+    """The same densities as full values."""
+    a, b = gpbc_density_offsets(p, nx)
+    return 1.0 + a, 1.0 + b
 
 
 def to_params(p, nx: int | None = None) -> OrcParams:
@@ -115,7 +121,7 @@ def to_params(p, nx: int | None = None) -> OrcParams:
     u_wall."""
     get = (lambda k, d=None: p.get(k, d)) if isinstance(p, dict) else (lambda k, d=None: getattr(p, k, d))
     gpbc = get("x_mode", "periodic") == "gpbc"
-    rin, rout = gpbc_densities(p, nx) if gpbc else (0.0, 0.0)
+    rin, rout = gpbc_density_offsets(p, nx) if gpbc else (0.0, 0.0)
     return OrcParams(float(get("tau_lb")), float(get("g_x", 0.0)), float(get("G_inf", 0.0)),
                      float(get("tau0", 0.0)), float(get("theta", 0.0)), float(get("gamma_c", np.inf)),
                      float(get("rho0", 1.0)), int(get("stress_mode", 0)), 1 if gpbc else 0, rin, rout,

@@ -88,8 +88,9 @@ typedef struct {
     double rho0;    /* reference density in eta^N = rho0 c_s^2 (tau_LB - 1/2)       */
     int stress_mode;/* 0: instantaneous nlM (Eq. sigtsum); 1: backward Euler of Eq. (gkder) */
     int boundary;   /* 0: periodic x, body force g_x; 1: generalized periodic boundaries (GPBC) */
-    double rho_in;  /* GPBC: c_s^-2 p_+, the lattice density imposed at the inlet (x = -1)    */
-    double rho_out; /* GPBC: c_s^-2 p_-, the lattice density imposed at the outlet (x = nx)   */
+    double rho_in;  /* GPBC: c_s^-2 p_+ - 1, the lattice density imposed at the inlet (x = -1),
+                       as an offset from 1 like the populations                              */
+    double rho_out; /* GPBC: c_s^-2 p_- - 1 at the outlet (x = nx)                            */
     int top_wall;   /* 0: half-way bounce-back; 1: wall on row ny-1 moving with u_wall (Zou-He) */
     int pad_;
     double u_wall;  /* tangential velocity of the moving wall                                   */
@@ -419,7 +420,8 @@ static void node_update(const orc_params *p, int nx, int ny, int x, int y,
 
 /* Generalized periodic boundaries (Sec. II B): per boundary column (0: x = 0, 1: x = nx-1) the
  * density and momentum of every node's post-collision populations and the column mean of the
- * density.  colrho/coljx/coljy: [2][ny]; colmean: [2]. */
+ * density.  colrho/coljx/coljy: [2][ny]; colmean: [2].  Densities are kept as rho - 1 (sums of
+ * the population offsets), so that their rounding acts on the small part. */
 static void gpbc_columns(int nx, int ny, const double *dnstar, double *colrho, double *coljx,
                          double *coljy, double *colmean) {
     long N = (long)nx * ny;
@@ -427,7 +429,7 @@ static void gpbc_columns(int nx, int ny, const double *dnstar, double *colrho, d
         int x = c == 0 ? 0 : nx - 1;
         double sum = 0.0;
         for (int y = 0; y < ny; ++y) {
-            double r = 1.0, jx = 0.0, jy = 0.0;
+            double r = 0.0, jx = 0.0, jy = 0.0;
             for (int i = 0; i < 9; ++i) {
                 double v = dnstar[i * N + idx(nx, x, y)];
                 r += v;
@@ -450,11 +452,11 @@ static double gpbc_ghost(const orc_params *p, int i, int entering_inlet, int ny,
                          const double *colrho, const double *coljx, const double *coljy,
                          const double *colmean) {
     int c = entering_inlet ? 1 : 0; /* the column the population leaves */
-    double rho_s = colrho[c * ny + ys], jx = coljx[c * ny + ys], jy = coljy[c * ny + ys];
-    double rho_t = (entering_inlet ? p->rho_in : p->rho_out) + rho_s - colmean[c];
+    double rs_m1 = colrho[c * ny + ys], jx = coljx[c * ny + ys], jy = coljy[c * ny + ys];
+    double rt_m1 = (entering_inlet ? p->rho_in : p->rho_out) + rs_m1 - colmean[c]; /* offsets */
     double eq_t[9], eq_s[9];
-    orc_equilibrium_offset(rho_t - 1.0, jx / rho_t, jy / rho_t, eq_t);
-    orc_equilibrium_offset(rho_s - 1.0, jx / rho_s, jy / rho_s, eq_s);
+    orc_equilibrium_offset(rt_m1, jx / (1.0 + rt_m1), jy / (1.0 + rt_m1), eq_t);
+    orc_equilibrium_offset(rs_m1, jx / (1.0 + rs_m1), jy / (1.0 + rs_m1), eq_s);
     return eq_t[i] + (dnstar_s - eq_s[i]);
 }
 

@@ -202,8 +202,8 @@ __global__ void k_apply_gx(ChanParams<C>* chan, const double* gx, int n_ch, int 
     chan[c].u_wall = (C)gx[n_ch + c];  // staged after the forces: the moving-wall velocities
     if (chan[c].gpbc) {  // pressure-driven: g sets the ghost densities, there is no body force
         const double half = 1.5 * gx[c] * (double)(nx + 1);
-        chan[c].rho_in = (C)((double)chan[c].rho_ref + half);
-        chan[c].rho_out = (C)((double)chan[c].rho_ref - half);
+        chan[c].rho_in = (C)((double)chan[c].rho0_m1 + half);
+        chan[c].rho_out = (C)((double)chan[c].rho0_m1 - half);
     } else {
         chan[c].gx = (C)gx[c];
     }
@@ -363,7 +363,7 @@ std::vector<ChanParams<C>> make_chan(const lb_handle* h) {
         q.inv_gc = std::isinf(p.gamma_c) ? C(0) : (C)(1.0 / p.gamma_c);
         q.cD = (C)(p.G_inf * p.tau0 - p.rho0 * (p.tau_lb - 0.5) / 3.0);
         q.kdr = C(1);
-        q.rho_ref = (C)p.rho0;
+        q.rho0_m1 = (C)(p.rho0 - 1.0);
         q.moving = h->moving ? 1 : 0;
         q.u_wall = (C)h->u_wall[c];
         if (h->gpbc) {
@@ -373,8 +373,8 @@ std::vector<ChanParams<C>> make_chan(const lb_handle* h) {
             q.row_off = h->row_off[c];
             q.kdr = C(0);
             q.gx = C(0);
-            q.rho_in = (C)(p.rho0 + 1.5 * p.g_x * (double)(h->nx + 1));
-            q.rho_out = (C)(p.rho0 - 1.5 * p.g_x * (double)(h->nx + 1));
+            q.rho_in = (C)((p.rho0 - 1.0) + 1.5 * p.g_x * (double)(h->nx + 1));
+            q.rho_out = (C)((p.rho0 - 1.0) - 1.5 * p.g_x * (double)(h->nx + 1));
         }
         v[c] = q;
     }

@@ -115,9 +115,9 @@ struct ChanParams {
     C inv_gc;   // 1/gamma_c (0 = no shear thinning)
     C cD;       // eta_inf - eta^N = G tau0 - rho0 (tau_LB - 1/2)/3: Sigma^nN = sigma + cD D
     C kdr;      // 1 with the flow-induced density of Eq. (rhoplus); 0 under GPBC (Sec. II B)
-    C rho_ref;  // rho0
-    C rho_in;   // GPBC: c_s^-2 p_+ at the inlet ghost column x = -1
-    C rho_out;  // GPBC: c_s^-2 p_- at the outlet ghost column x = nx
+    C rho0_m1;  // rho0 - 1
+    C rho_in;   // GPBC: c_s^-2 p_+ - 1 at the inlet ghost column x = -1 (densities near 1 are kept
+    C rho_out;  //       as offsets from 1, like the populations); c_s^-2 p_- - 1 at x = nx
     C u_wall;   // tangential velocity of the moving wall (moving == 1)
 };
 
@@ -158,8 +158,8 @@ struct StepArgs {
     C guard;                       // |u| above which a channel is declared unstable
     uint32_t sr_key;               // per-step key of the stochastic rounding (F_SR)
     const C* __restrict__ gcol;    // GPBC boundary columns of pin (null: periodic x), layout
-                                   // [comp rho, jx, jy][col 0: x = 0, 1: x = nx-1][row], then
-                                   // the column means [channel][col]
+                                   // [comp rho - 1, jx, jy][col 0: x = 0, 1: x = nx-1][row], then
+                                   // the column means of rho - 1 [channel][col]
     int gny;                       // rows of all channels (the row stride of gcol)
 };
 
@@ -205,7 +205,8 @@ __device__ __forceinline__ void gradient_velocity(const C (&d)[9], C gx, C& dR, 
 // n*_i + w_i [delta - (4.5 (c.j)^2 - 1.5 j^2) delta / (rho_s (rho_s + delta))].  rho_s and j_s
 // are the moments of the node's post-collision populations (the shortened forcing keeps both).
 template <typename C>
-__device__ __forceinline__ C gpbc_shift(int i, C rho_s, C jx, C jy, C delta) {
+__device__ __forceinline__ C gpbc_shift(int i, C rho_s_m1, C jx, C jy, C delta) {
+    const C rho_s = C(1) + rho_s_m1;
     const C cj = C(cx(i)) * jx + C(cy(i)) * jy;
     const C q = C(4.5) * cj * cj - C(1.5) * (jx * jx + jy * jy);
     return wgt<C>(i) * (delta - q * Arith<C>::div(delta, rho_s * (rho_s + delta)));

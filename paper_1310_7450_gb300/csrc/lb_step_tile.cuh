@@ -19,7 +19,7 @@ namespace lbk {
 // Boundary data of one channel: GPBC columns (col == nullptr: periodic x) and the moving wall.
 template <typename C>
 struct GpbcView {
-    const C* col;  // gcol + row_off: rho at [c * gny + y], jx at [(2 + c) * gny + y], jy at [(4 + c) * gny + y]
+    const C* col;  // gcol + row_off: rho - 1 at [c * gny + y], jx at [(2 + c) * gny + y], jy at [(4 + c) * gny + y]
     int gny;
     C dplus;       // rho_in - mean rho of the outlet column (populations entering at x = 0)
     C dminus;      // rho_out - mean rho of the inlet column (populations entering at x = nx-1)
@@ -240,8 +240,8 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
 }
 
 // GPBC boundary columns of the stored state: per node of the columns x = 0 and x = nx-1 the
-// density and momentum of its post-collision populations, and per column the mean density
-// (a fixed-order block reduction, so every step kernel sees the same value).  One CTA per
+// density (as rho - 1) and momentum of its post-collision populations, and per column the mean
+// of rho - 1 (a fixed-order block reduction, so every step kernel sees the same value).  One CTA per
 // (channel, column); channels without GPBC are skipped.
 template <typename T, typename C, int NT>
 __global__ void __launch_bounds__(NT) k_gpbc_columns(const T* __restrict__ pin, const ChanParams<C>* __restrict__ chan,
@@ -259,11 +259,10 @@ __global__ void __launch_bounds__(NT) k_gpbc_columns(const T* __restrict__ pin, 
         for (int i = 0; i < 9; ++i) d[i] = Store<T>::ld(pc + (long long)i * P.P + (long long)y * nx + x);
         C dR, jx, jy;
         moments<C>(d, dR, jx, jy);
-        const C rho = C(1) + dR;
-        col[c * gny + y] = rho;
+        col[c * gny + y] = dR;
         col[(2 + c) * gny + y] = jx;
         col[(4 + c) * gny + y] = jy;
-        sum += (double)rho;
+        sum += (double)dR;
     }
     __shared__ double red[NT];
     red[threadIdx.x] = sum;

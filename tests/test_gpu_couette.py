@@ -88,7 +88,8 @@ def test_couette_with_pressure_driven_ends(stream):
     st = oracle.init_state(inputs.linear_density(nx, ny, rin, rout))
     oracle.run(pg, st, 3000)
     u_o, s_o, r_o = oracle.fields(pg, st)
-    assert rel(u_g, u_o) < 1e-12 and rel(s_g, s_o) < 1e-11 and rel(r_g - 1, r_o - 1) < 1e-11
+    assert rel(u_g, u_o) < 1e-12 and rel(s_g, s_o) < 1e-11
+    assert np.abs(r_g - r_o).max() < 2e-15   # rho ~ 1: a few units of its last place
 
 
 def test_wall_velocity_needs_a_moving_wall(stream):
