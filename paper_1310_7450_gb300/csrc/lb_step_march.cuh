@@ -223,7 +223,9 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             for (int r = rbase; r < rbase + K && r <= rlast; ++r) issue(idx_of(r), x0, r);
         }
         nload = L0 + (uint32_t)(rlast - rbase + 1);
-        double r_du2 = 0.0, r_u2 = 0.0, r_ux = 0.0, r_umax2 = 0.0;  // residual partials (F_RESID)
+        // residual partials (F_RESID) of this thread's column, in the arithmetic type (a few
+        // hundred rows at most); the block reduction below runs in double
+        C r_du2 = C(0), r_u2 = C(0), r_ux = C(0), r_umax2 = C(0);
         C dcur[9], dnext[9];
         C dRc = 0, jxc = 0, jyc = 0, dRn = 0, jxn = 0, jyn = 0;
         bool ok = true;
@@ -327,11 +329,11 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                     const C urx = jxc * ih, ury = jyc * ih;
                     C* up_ = a.uprev + 2 * P.base;
                     if (a.flags & F_RESID) {
-                        const double dx_ = (double)urx - (double)up_[pn], dy_ = (double)ury - (double)up_[P.P + pn];
-                        const double u2 = (double)urx * urx + (double)ury * ury;
+                        const C dx_ = urx - up_[pn], dy_ = ury - up_[P.P + pn];
+                        const C u2 = urx * urx + ury * ury;
                         r_du2 += dx_ * dx_ + dy_ * dy_;
                         r_u2 += u2;
-                        r_ux += (double)urx;
+                        r_ux += urx;
                         r_umax2 = fmax(r_umax2, u2);
                     }
                     if (a.flags & F_SAVE_U) {
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         __syncthreads();  // every slot read of this item is done before the next item's copies
         if (!bad && (a.flags & F_RESID)) {
             // block reduction of (sum du^2, sum u^2, sum u_x, max |u|) into this item's partials
-            double v[4] = {r_du2, r_u2, r_ux, r_umax2};
+            double v[4] = {(double)r_du2, (double)r_u2, (double)r_ux, (double)r_umax2};
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
