@@ -248,6 +248,19 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         // the stored flow-induced density, loaded two rows ahead of its use
         C drho_next = a.drho[P.base + (long long)y0 * nx + x];
         C drho_next2 = (y0 + 1 < y1) ? a.drho[P.base + (long long)(y0 + 1) * nx + x] : C(0);
+        // on residual steps the saved velocity of each row is prefetched the same way
+        const bool resid = (a.flags & F_RESID) != 0;
+        const C* upx = a.uprev + 2 * P.base + x;
+        const C* upy = upx + P.P;
+        C upx_next = C(0), upy_next = C(0), upx_next2 = C(0), upy_next2 = C(0);
+        if (resid) {
+            upx_next = upx[(long long)y0 * nx];
+            upy_next = upy[(long long)y0 * nx];
+            if (y0 + 1 < y1) {
+                upx_next2 = upx[(long long)(y0 + 1) * nx];
+                upy_next2 = upy[(long long)(y0 + 1) * nx];
+            }
+        }
         __syncthreads();
         if (t == 0) {
             fence_proxy_async();
@@ -268,6 +281,15 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             const C drho_prev = drho_next;
             drho_next = drho_next2;
             if (y + 2 < y1) drho_next2 = a.drho[P.base + (long long)(y + 2) * nx + x];
+            const C upx_cur = upx_next, upy_cur = upy_next;
+            if (resid) {
+                upx_next = upx_next2;
+                upy_next = upy_next2;
+                if (y + 2 < y1) {
+                    upx_next2 = upx[(long long)(y + 2) * nx];
+                    upy_next2 = upy[(long long)(y + 2) * nx];
+                }
+            }
             __syncthreads();
             if (s_bad) { bad = true; break; }
             // 2. refill the slot of row y (no longer read) with row y+K
@@ -329,7 +351,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                     const C urx = jxc * ih, ury = jyc * ih;
                     C* up_ = a.uprev + 2 * P.base;
                     if (a.flags & F_RESID) {
-                        const C dx_ = urx - up_[pn], dy_ = ury - up_[P.P + pn];
+                        const C dx_ = urx - upx_cur, dy_ = ury - upy_cur;
                         const C u2 = urx * urx + ury * ury;
                         r_du2 += dx_ * dx_ + dy_ * dy_;
                         r_u2 += u2;
