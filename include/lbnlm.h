@@ -208,6 +208,15 @@ lb_status lb_sweep_tune(lb_handle *h);
  * tuning run (ms for 256 steps of every channel). */
 lb_status lb_sweep_config(lb_handle *h, int *threads, int *cluster, double *tune_ms);
 
+/* Which sweep kernel the tuned (or set) configuration uses: 0 = the state streamed through L2
+ * every step (k_sweep), 1 = the state resident in the cluster's shared memory, halo rows read from
+ * the neighbouring CTAs (k_sweep_smem; needs ny / cluster >= 3 for every channel).  -1: null. */
+int lb_sweep_variant(const lb_handle *h);
+
+/* Fix the sweep configuration instead of tuning it (variant 0/1, threads 128/256, cluster size
+ * 1..16); LB_EINVAL if it does not fit every channel of the handle. */
+lb_status lb_sweep_set_config(lb_handle *h, int variant, int threads, int cluster);
+
 /* Allocation-free diagnostics.  The paper has no counterpart: this is a service for callers that
  * must not allocate device memory when they ask for the convergence measures -- e.g. a monitoring
  * loop that cannot take cudaMalloc's implicit device synchronisation mid-run, or a process whose

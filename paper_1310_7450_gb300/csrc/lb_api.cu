@@ -21,6 +21,7 @@
 #include "lb_step_march.cuh"
 #include "lb_step_tile.cuh"
 #include "lb_sweep.cuh"
+#include "lb_sweep_smem.cuh"
 #include "lbnlm.h"
 
 namespace lbk {
@@ -45,6 +46,13 @@ LB_SWEEP_EXTERN(float, float)
 LB_SWEEP_EXTERN(__nv_bfloat16, float)
 LB_SWEEP_EXTERN(double, double)
 #undef LB_SWEEP_EXTERN
+#define LB_SWEEP_SMEM_EXTERN(T, C)                                                                                   \
+    extern template cudaError_t launch_sweep_smem<T, C, 128, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_sweep_smem<T, C, 256, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t);
+LB_SWEEP_SMEM_EXTERN(float, float)
+LB_SWEEP_SMEM_EXTERN(__nv_bfloat16, float)
+LB_SWEEP_SMEM_EXTERN(double, double)
+#undef LB_SWEEP_SMEM_EXTERN
 extern template cudaError_t march_occupancy<float, float, 0>(int*);
 extern template cudaError_t march_occupancy<float, float, 1>(int*);
 extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0>(int*);
@@ -322,6 +330,7 @@ struct lb_handle {
     double* sweep_res_d = nullptr;
     int* sweep_order_d = nullptr;
     int sweep_nt = 0, sweep_cl = 0;     // tuned configuration (0: not tuned yet)
+    int sweep_var = 0;                  // 0: state streamed through L2, 1: state in shared memory
     double sweep_tune_ms = 0.0;
     MarchItem* march_items_d = nullptr;
     int* march_item_begin_d = nullptr;  // {0, n_march_items}: the residual reduction's item range
@@ -785,9 +794,24 @@ size_t sweep_smem(const lb_handle* h, int cl) {
     const int rows = (sweep_max_ny(h) + cl - 1) / cl + 4;
     return (size_t)rows * h->nx * 2 * h->csize;
 }
+int sweep_min_ny(const lb_handle* h) {
+    int m = 1 << 30;
+    for (int c = 0; c < h->n_ch; ++c) m = std::min(m, h->ny[c]);
+    return m;
+}
+// Shared-memory resident variant: every CTA owns >= 3 rows (halo rows come from the neighbours),
+// and its rows, halos and velocity rows fit the 227 KB of one CTA.
+size_t sweep_smem_resident(const lb_handle* h, int cl) {
+    const int rows = (sweep_max_ny(h) + cl - 1) / cl;
+    const size_t pops = ((size_t)2 * 9 * (rows + 6) * h->nx * h->tsize + 15) / 16 * 16;
+    return pops + (size_t)(rows + 4) * h->nx * 2 * h->csize;
+}
+bool sweep_smem_fits(const lb_handle* h, int nt, int cl) {
+    return sweep_fits(h, nt, cl) && sweep_min_ny(h) / cl >= 3 && sweep_smem_resident(h, cl) <= 227 * 1024;
+}
 
 template <typename T, typename C>
-cudaError_t sweep_launch(lb_handle* h, int nt, int cl, int n_clusters, double tol, int check, long long max_steps) {
+cudaError_t sweep_launch(lb_handle* h, int var, int nt, int cl, int n_clusters, double tol, int check, long long max_steps) {
     SweepArgs<T, C> a{};
     a.popA = (T*)h->popA;
     a.popB = (T*)h->popB;
@@ -804,16 +828,22 @@ cudaError_t sweep_launch(lb_handle* h, int nt, int cl, int n_clusters, double to
     a.tol = tol;
     a.sr = (h->flags & LB_GRID_BF16_STOCHASTIC) && h->prec == LB_PREC_BF16;
     a.sr_key = step_key(h, h->step + 0x5bd1e995ll);
+    if (var == 1) {
+        const size_t smem = sweep_smem_resident(h, cl);
+        if (nt == 128) return launch_sweep_smem<T, C, 128, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
+        return launch_sweep_smem<T, C, 256, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
+    }
     const size_t smem = sweep_smem(h, cl);
     if (nt == 128) return launch_sweep<T, C, 128, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
     return launch_sweep<T, C, 256, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
 }
 
-cudaError_t sweep_launch_any(lb_handle* h, int nt, int cl, int n_clusters, double tol, int check, long long max_steps) {
+cudaError_t sweep_launch_any(lb_handle* h, int var, int nt, int cl, int n_clusters, double tol, int check,
+                             long long max_steps) {
     return with_types(h->prec, [&](auto tt, auto tc) -> cudaError_t {
         LB_TYPES(tt, tc);
         if constexpr (std::is_same<T, double>::value != std::is_same<C, double>::value) return cudaErrorNotSupported;
-        else return sweep_launch<T, C>(h, nt, cl, n_clusters, tol, check, max_steps);
+        else return sweep_launch<T, C>(h, var, nt, cl, n_clusters, tol, check, max_steps);
     });
 }
 
@@ -840,11 +870,13 @@ lb_status sweep_order(lb_handle* h, int* n_active) {
 // Autotuner: time a short sweep (no channel can converge: tol < 0) for every (threads, cluster
 // size) that fits, from the same saved state, and keep the fastest.  The state is restored.
 lb_status sweep_tune(lb_handle* h, int n_active) {
-    struct Cand { int nt, cl; };
+    struct Cand { int var, nt, cl; };
     std::vector<Cand> cands;
     for (int nt : {128, 256})
-        for (int cl : {1, 2, 4, 8, 16})
-            if (sweep_fits(h, nt, cl) && sweep_smem(h, cl) <= 200 * 1024) cands.push_back({nt, cl});
+        for (int cl : {1, 2, 4, 8, 16}) {
+            if (sweep_fits(h, nt, cl) && sweep_smem(h, cl) <= 200 * 1024) cands.push_back({0, nt, cl});
+            if (sweep_smem_fits(h, nt, cl)) cands.push_back({1, nt, cl});
+        }
     if (cands.empty()) return fail(LB_EINVAL, "lb_run_until_steady: a channel is too wide for the sweep kernel%s");
     const size_t pop_b = 9 * h->planes * h->tsize, dr_b = h->planes * h->csize, up_b = 2 * h->planes * h->csize;
     void* save = nullptr;
@@ -866,18 +898,28 @@ lb_status sweep_tune(lb_handle* h, int n_active) {
     for (const Cand& c : cands) {
         if (e != cudaSuccess) break;
         float ms = 0.f;
-        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
+        bool launched = true;
+        for (int rep = 0; rep < 2 && e == cudaSuccess && launched; ++rep) {  // first run warms up
             e = restore();
             if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-            if (e == cudaSuccess) e = sweep_launch_any(h, c.nt, c.cl, n_active, -1.0, 16, 256);
+            if (e == cudaSuccess) {
+                // a cluster shape the device cannot co-schedule is refused at launch (a
+                // configuration error that leaves the context usable): skip the candidate
+                const cudaError_t le = sweep_launch_any(h, c.var, c.nt, c.cl, n_active, -1.0, 16, 256);
+                if (le != cudaSuccess) {
+                    launched = false;
+                    (void)cudaGetLastError();
+                }
+            }
             if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         }
-        if (e == cudaSuccess && ms < best) {
+        if (e == cudaSuccess && launched && ms < best) {
             best = ms;
             h->sweep_nt = c.nt;
             h->sweep_cl = c.cl;
+            h->sweep_var = c.var;
         }
     }
     if (e == cudaSuccess) e = restore();
@@ -886,6 +928,7 @@ lb_status sweep_tune(lb_handle* h, int n_active) {
     if (e1) cudaEventDestroy(e1);
     cudaFree(save);
     if (e != cudaSuccess) { h->sweep_nt = h->sweep_cl = 0; return cuda_fail(e, "lb_run_until_steady: autotune"); }
+    if (best == 1e300) { h->sweep_nt = h->sweep_cl = 0; return fail(LB_ECUDA, "lb_run_until_steady: no sweep configuration could be launched%s"); }
     h->sweep_tune_ms = best;
     return LB_OK;
 }
@@ -918,7 +961,7 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
         }
         std::vector<long long> init(h->n_ch, -3);
         LB_CK(cudaMemcpy(h->sweep_steps_d, init.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice));
-        LB_CK(sweep_launch_any(h, h->sweep_nt, h->sweep_cl, n_active, tol, (int)check_every, ms));
+        LB_CK(sweep_launch_any(h, h->sweep_var, h->sweep_nt, h->sweep_cl, n_active, tol, (int)check_every, ms));
         LB_CK(cudaMemcpyAsync(steps.data(), h->sweep_steps_d, sizeof(long long) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
         LB_CK(cudaMemcpyAsync(res.data(), h->sweep_res_d, sizeof(double) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
         LB_CK(cudaStreamSynchronize(h->stream));
@@ -941,6 +984,21 @@ lb_status lb_sweep_tune(lb_handle* h) {
     lb_status st = sweep_order(h, &n_active);
     if (st != LB_OK || n_active == 0) return st;
     return sweep_tune(h, n_active);
+}
+
+int lb_sweep_variant(const lb_handle* h) { return h ? h->sweep_var : -1; }
+
+lb_status lb_sweep_set_config(lb_handle* h, int variant, int threads, int cluster) {
+    if (!h || (variant != 0 && variant != 1) || (threads != 128 && threads != 256))
+        return fail(LB_EINVAL, "lb_sweep_set_config: variant 0/1 and threads 128/256%s");
+    const bool ok = variant == 0 ? (sweep_fits(h, threads, cluster) && sweep_smem(h, cluster) <= 200 * 1024)
+                                 : sweep_smem_fits(h, threads, cluster);
+    if (cluster < 1 || cluster > 16 || !ok) return fail(LB_EINVAL, "lb_sweep_set_config: configuration does not fit these channels%s");
+    h->sweep_var = variant;
+    h->sweep_nt = threads;
+    h->sweep_cl = cluster;
+    h->sweep_tune_ms = 0.0;
+    return LB_OK;
 }
 
 lb_status lb_sweep_config(lb_handle* h, int* threads, int* cluster, double* tune_ms) {

@@ -92,6 +92,8 @@ def load():
         "lb_mlp_set_params": ([_H, c_void_p], c_int),
         "lb_run_until_steady": ([_H, c_double, c_long, c_long, c_void_p, c_void_p], c_int),
         "lb_sweep_config": ([_H, POINTER(c_int), POINTER(c_int), POINTER(c_double)], c_int),
+        "lb_sweep_variant": ([_H], c_int),
+        "lb_sweep_set_config": ([_H, c_int, c_int, c_int], c_int),
         "lb_sweep_tune": ([_H], c_int),
         "lb_field_monitor_static": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p], c_int),
         "lb_uses_row_march": ([_H], c_int),
@@ -244,6 +246,14 @@ def lb_sweep_config(h: int):
     nt, cl, ms = c_int(), c_int(), c_double()
     _check(load().lb_sweep_config(h, ctypes.byref(nt), ctypes.byref(cl), ctypes.byref(ms)), "lb_sweep_config")
     return nt.value, cl.value, ms.value
+
+
+def lb_sweep_variant(h: int) -> int:
+    return int(load().lb_sweep_variant(h))
+
+
+def lb_sweep_set_config(h: int, variant: int, threads: int, cluster: int):
+    _check(load().lb_sweep_set_config(h, int(variant), int(threads), int(cluster)), "lb_sweep_set_config")
 
 
 def lb_mlp_create(n_in: int, width: int, n_out: int, max_batch: int, seed: int = 0, stream=None) -> int:

@@ -90,3 +90,80 @@ def test_sweep_retires_unstable_channel(stream):
         status = sim.status()
     assert steps[0] == -1 and steps[1] == -2
     assert list(status) == [0, 1]
+
+
+def force_variant(sim, variant):
+    """Fix the sweep kernel (0: state through L2, 1: state in the cluster's shared memory) with the
+    first configuration that fits."""
+    for cl in (1, 2, 4, 8, 16):
+        for nt in (128, 256):
+            try:
+                lbnlm.lb_sweep_set_config(sim.h, variant, nt, cl)
+                assert lbnlm.lb_sweep_variant(sim.h) == variant
+                return nt, cl
+            except lbnlm.LBError:
+                pass
+    pytest.fail("no sweep configuration fits")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_shared_memory_sweep_equals_l2_sweep_and_lb_step(stream, prec):
+    """The shared-memory resident sweep computes the same per-node arithmetic as the L2-streamed
+    one and as lb_step: the states after 200 steps agree bitwise (f32 / bf16 / f64 storage), for a
+    cluster of several CTAs whose halo rows travel through distributed shared memory."""
+    nys = [24, 80, 13, 40]
+    ps = channel_set(nys, 70)
+    out = []
+    for variant in (0, 1):
+        with lbnlm.Channels(4, nys, ps, prec, stream=stream) as sim:
+            nt, cl = force_variant(sim, variant)
+            steps, _ = sim.run_until_steady(-1.0, check_every=10, max_steps=200)
+            assert list(steps) == [-1] * len(nys)
+            out.append(sim.populations())
+    with lbnlm.Channels(4, nys, ps, prec, stream=stream) as sim:
+        sim.step(200)
+        out.append(sim.populations())
+    for k in range(len(nys)):
+        assert np.array_equal(out[0][k][0], out[1][k][0]) and np.array_equal(out[0][k][1], out[1][k][1])
+        assert rel(out[1][k][0], out[2][k][0]) < (1e-14 if prec == "f64" else 1e-6)
+
+
+def test_shared_memory_sweep_multi_cta_clusters(stream):
+    """Clusters of 4 CTAs per channel (rows split 4 ways, three halo rows from each neighbour)."""
+    nys = [16, 29, 64]
+    ps = channel_set(nys, 80)
+    res = []
+    for variant in (0, 1):
+        with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim:
+            lbnlm.lb_sweep_set_config(sim.h, variant, 128, 4)
+            sim.run_until_steady(-1.0, check_every=10, max_steps=300)
+            res.append(sim.populations())
+    for k in range(len(nys)):
+        assert np.array_equal(res[0][k][0], res[1][k][0])
+
+
+def test_shared_memory_sweep_converges_and_retires(stream):
+    nys = [12, 20, 28]
+    ps = [dict(inputs.matched_params(0.9, 0.0, 0.1, 1e-3, 1e-6)) for _ in nys]
+    got = []
+    for variant in (0, 1):
+        with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim:
+            force_variant(sim, variant)
+            steps, r = sim.run_until_steady(1e-8, check_every=50, max_steps=10**6)
+            got.append((steps, r, sim.populations()))
+    assert np.array_equal(got[0][0], got[1][0])
+    assert np.abs(got[0][1] / got[1][1] - 1).max() < 1e-9
+    for k in range(len(nys)):
+        assert np.array_equal(got[0][2][k][0], got[1][2][k][0])
+    nys = [16, 16]
+    ps = channel_set(nys, 60)
+    with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim:
+        pops = sim.populations()
+        n1 = pops[1][0].copy()
+        n1[2, 4, 1] = np.nan
+        sim.set_populations([pops[0][0], n1], [pops[0][1], pops[1][1]])
+        force_variant(sim, 1)
+        steps, res = sim.run_until_steady(-1.0, check_every=10, max_steps=100)
+        status = sim.status()
+    assert steps[0] == -1 and steps[1] == -2
+    assert list(status) == [0, 1]
