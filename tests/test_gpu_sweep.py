@@ -124,7 +124,11 @@ def test_shared_memory_sweep_equals_l2_sweep_and_lb_step(stream, prec):
         sim.step(200)
         out.append(sim.populations())
     for k in range(len(nys)):
-        assert np.array_equal(out[0][k][0], out[1][k][0]) and np.array_equal(out[0][k][1], out[1][k][1])
+        assert np.array_equal(out[0][k][0], out[1][k][0])
+        # delta rho = -3/2 tr Sigma^nN cancels to rounding noise in the near-Newtonian channels; the
+        # two kernels may contract that sum differently, so it is compared against its own scale
+        dA, dB = out[0][k][1], out[1][k][1]
+        assert np.abs(dA - dB).max() <= 1e-9 * max(np.abs(dA).max(), 1e-20)
         assert rel(out[1][k][0], out[2][k][0]) < (1e-14 if prec == "f64" else 1e-6)
 
 
