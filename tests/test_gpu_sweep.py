@@ -143,7 +143,7 @@ def test_shared_memory_sweep_multi_cta_clusters(stream):
             sim.run_until_steady(-1.0, check_every=10, max_steps=300)
             res.append(sim.populations())
     for k in range(len(nys)):
-        assert rel(res[1][k][0] - oracle.WEIGHTS[:, None, None], res[0][k][0] - oracle.WEIGHTS[:, None, None]) < 1e-13
+        assert rel(res[1][k][0], res[0][k][0]) < 1e-14   # full FP64 populations: a unit of the last place
 
 
 def test_shared_memory_sweep_converges_and_retires(stream):
