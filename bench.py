@@ -407,6 +407,8 @@ def run_sweep(args):
     tune_s = time.perf_counter() - t0
     nt, cl, tune_ms = lbnlm.lb_sweep_config(sim.h)
     variant = ("l2", "shared_memory")[lbnlm.lb_sweep_variant(sim.h)]
+    classes = [{"kernel": ("l2", "shared_memory")[v], "threads": t, "cluster": c, "channels": k}
+               for v, t, c, k in lbnlm.lb_sweep_groups(sim.h)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     steps, res = sim.run_until_steady(args.tol, check_every=args.check, max_steps=args.max_steps)
@@ -438,7 +440,8 @@ def run_sweep(args):
             "converged": int(conv.sum()), "channels": len(nys), "max_steps_taken": int(steps.max()),
             "steps_percentiles": [int(v) for v in np.percentile(steps[conv], [0, 50, 90, 100])] if conv.any() else None,
             "node_steps": int(sum(max(steps[c], 0) * 4 * nys[c] for c in range(len(nys)))),
-            "autotune": {"kernel": variant, "threads": nt, "cluster": cl, "tune_run_ms": tune_ms, "tune_wall_s": tune_s},
+            "autotune": {"kernel": variant, "threads": nt, "cluster": cl, "tune_run_ms": tune_ms, "tune_wall_s": tune_s,
+                         "classes": classes},
             "baseline_plain_per_channel": {"estimated_s": est, "sample_channels": len(per_step),
                                            "per_step_us_by_ny": {str(nys[c]): round(1e6 * v, 2) for c, v in per_step.items()}},
             "speedup_vs_plain": est / wall if wall > 0 else None}

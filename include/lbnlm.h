@@ -208,13 +208,19 @@ lb_status lb_sweep_tune(lb_handle *h);
  * tuning run (ms for 256 steps of every channel). */
 lb_status lb_sweep_config(lb_handle *h, int *threads, int *cluster, double *tune_ms);
 
-/* Which sweep kernel the tuned (or set) configuration uses: 0 = the state streamed through L2
- * every step (k_sweep), 1 = the state resident in the cluster's shared memory, halo rows read from
- * the neighbouring CTAs (k_sweep_smem; needs ny / cluster >= 3 for every channel).  -1: null. */
+/* The sweep runs the stable channels in width classes (floor(log2 ny)), one persistent launch per
+ * class on forked streams, each class with its own configuration: kernel variant 0 = the state
+ * streamed through L2 every step (k_sweep), 1 = the state resident in the cluster's shared memory,
+ * halo rows read from the neighbouring CTAs (k_sweep_smem; needs ny / cluster >= 3); threads per
+ * CTA; CTAs per cluster.  lb_sweep_groups writes up to max_groups entries (any pointer may be NULL;
+ * threads 0 = not tuned yet) and returns the number of classes (-1: null handle).
+ * lb_sweep_config reports the widest class and the summed tuning time; lb_sweep_variant the
+ * widest class's kernel (-1 before the first tuning / setting). */
+int lb_sweep_groups(const lb_handle *h, int *variant, int *threads, int *cluster, int *channels, int max_groups);
 int lb_sweep_variant(const lb_handle *h);
 
-/* Fix the sweep configuration instead of tuning it (variant 0/1, threads 128/256, cluster size
- * 1..16); LB_EINVAL if it does not fit every channel of the handle. */
+/* Fix one configuration for every class instead of tuning (variant 0/1, threads 128/256, cluster
+ * size 1..16); LB_EINVAL if it does not fit every class of the handle. */
 lb_status lb_sweep_set_config(lb_handle *h, int variant, int threads, int cluster);
 
 /* Allocation-free diagnostics.  The paper has no counterpart: this is a service for callers that

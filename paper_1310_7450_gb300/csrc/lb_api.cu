@@ -279,6 +279,15 @@ auto with_types(int prec, F&& f) {
 
 }  // namespace
 
+// Channels of one width class in the batched sweep and the configuration they run with.
+struct SweepGroup {
+    int cls = 0;                    // floor(log2 ny)
+    int begin = 0, count = 0;       // range in the widest-first channel order
+    int ny_min = 0, ny_max = 0;
+    int var = 0, nt = 0, cl = 0;    // 0: state through L2, 1: state in shared memory; nt == 0: not tuned
+    double tune_ms = 0.0;
+};
+
 struct lb_handle {
     int dev = 0;
     cudaStream_t stream = nullptr;
@@ -329,9 +338,10 @@ struct lb_handle {
     long long* sweep_steps_d = nullptr;
     double* sweep_res_d = nullptr;
     int* sweep_order_d = nullptr;
-    int sweep_nt = 0, sweep_cl = 0;     // tuned configuration (0: not tuned yet)
-    int sweep_var = 0;                  // 0: state streamed through L2, 1: state in shared memory
-    double sweep_tune_ms = 0.0;
+    std::vector<SweepGroup> sweep_groups;  // width classes of the active channels and their configurations
+    std::vector<cudaStream_t> gstreams;     // forked streams of the class launches
+    std::vector<cudaEvent_t> gevents;
+    cudaEvent_t fork_ev = nullptr;
     MarchItem* march_items_d = nullptr;
     int* march_item_begin_d = nullptr;  // {0, n_march_items}: the residual reduction's item range
     int n_march_items = 0, march_grid = 0;
@@ -564,6 +574,9 @@ void release(lb_handle* h) {
     for (int k = 0; k < 2; ++k)
         if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (cudaStream_t q : h->gstreams) cudaStreamDestroy(q);
+    for (cudaEvent_t q : h->gevents) cudaEventDestroy(q);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     delete h;
 }
 
@@ -781,37 +794,37 @@ lb_status request_status(lb_handle* h) {
 
 constexpr int kSweepNPT = 4;  // nodes per thread of the sweep kernel
 
-int sweep_max_ny(const lb_handle* h) {
-    int m = 0;
-    for (int c = 0; c < h->n_ch; ++c) m = std::max(m, h->ny[c]);
-    return m;
+// Channels of one width class (floor(log2 ny)) run in their own persistent launch with their own
+// tuned configuration; the classes' launches run side by side on forked streams.
+int width_class(int ny) {
+    int k = 0;
+    while ((2 << k) <= ny) ++k;
+    return k;
 }
-bool sweep_fits(const lb_handle* h, int nt, int cl) {
-    const int rows = (sweep_max_ny(h) + cl - 1) / cl;
-    return (long long)rows * h->nx <= (long long)nt * kSweepNPT;
+bool sweep_fits(int ny_max, int nx, int nt, int cl) {
+    const int rows = (ny_max + cl - 1) / cl;
+    return (long long)rows * nx <= (long long)nt * kSweepNPT;
 }
-size_t sweep_smem(const lb_handle* h, int cl) {
-    const int rows = (sweep_max_ny(h) + cl - 1) / cl + 4;
+size_t sweep_smem(const lb_handle* h, int ny_max, int cl) {
+    const int rows = (ny_max + cl - 1) / cl + 4;
     return (size_t)rows * h->nx * 2 * h->csize;
-}
-int sweep_min_ny(const lb_handle* h) {
-    int m = 1 << 30;
-    for (int c = 0; c < h->n_ch; ++c) m = std::min(m, h->ny[c]);
-    return m;
 }
 // Shared-memory resident variant: every CTA owns >= 3 rows (halo rows come from the neighbours),
 // and its rows, halos and velocity rows fit the 227 KB of one CTA.
-size_t sweep_smem_resident(const lb_handle* h, int cl) {
-    const int rows = (sweep_max_ny(h) + cl - 1) / cl;
+size_t sweep_smem_resident(const lb_handle* h, int ny_max, int cl) {
+    const int rows = (ny_max + cl - 1) / cl;
     const size_t pops = ((size_t)2 * 9 * (rows + 6) * h->nx * h->tsize + 15) / 16 * 16;
     return pops + (size_t)(rows + 4) * h->nx * 2 * h->csize;
 }
-bool sweep_smem_fits(const lb_handle* h, int nt, int cl) {
-    return sweep_fits(h, nt, cl) && sweep_min_ny(h) / cl >= 3 && sweep_smem_resident(h, cl) <= 227 * 1024;
+bool sweep_config_fits(const lb_handle* h, const SweepGroup& g, int var, int nt, int cl) {
+    if (cl < 1 || cl > 16 || (nt != 128 && nt != 256) || !sweep_fits(g.ny_max, h->nx, nt, cl)) return false;
+    if (var == 0) return sweep_smem(h, g.ny_max, cl) <= 200 * 1024;
+    return g.ny_min / cl >= 3 && sweep_smem_resident(h, g.ny_max, cl) <= 227 * 1024;
 }
 
 template <typename T, typename C>
-cudaError_t sweep_launch(lb_handle* h, int var, int nt, int cl, int n_clusters, double tol, int check, long long max_steps) {
+cudaError_t sweep_launch(lb_handle* h, const SweepGroup& g, int var, int nt, int cl, double tol, int check,
+                         long long max_steps, cudaStream_t stream) {
     SweepArgs<T, C> a{};
     a.popA = (T*)h->popA;
     a.popB = (T*)h->popB;
@@ -819,7 +832,7 @@ cudaError_t sweep_launch(lb_handle* h, int var, int nt, int cl, int n_clusters, 
     a.uprev = (C*)h->uprev;
     a.chan = (const ChanParams<C>*)h->chan;
     a.status = h->status_d;
-    a.order = h->sweep_order_d;
+    a.order = h->sweep_order_d + g.begin;
     a.steps_out = h->sweep_steps_d;
     a.res_out = h->sweep_res_d;
     a.nx = h->nx;
@@ -829,25 +842,26 @@ cudaError_t sweep_launch(lb_handle* h, int var, int nt, int cl, int n_clusters, 
     a.sr = (h->flags & LB_GRID_BF16_STOCHASTIC) && h->prec == LB_PREC_BF16;
     a.sr_key = step_key(h, h->step + 0x5bd1e995ll);
     if (var == 1) {
-        const size_t smem = sweep_smem_resident(h, cl);
-        if (nt == 128) return launch_sweep_smem<T, C, 128, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
-        return launch_sweep_smem<T, C, 256, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
+        const size_t smem = sweep_smem_resident(h, g.ny_max, cl);
+        if (nt == 128) return launch_sweep_smem<T, C, 128, kSweepNPT>(a, g.count, cl, smem, stream);
+        return launch_sweep_smem<T, C, 256, kSweepNPT>(a, g.count, cl, smem, stream);
     }
-    const size_t smem = sweep_smem(h, cl);
-    if (nt == 128) return launch_sweep<T, C, 128, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
-    return launch_sweep<T, C, 256, kSweepNPT>(a, n_clusters, cl, smem, h->stream);
+    const size_t smem = sweep_smem(h, g.ny_max, cl);
+    if (nt == 128) return launch_sweep<T, C, 128, kSweepNPT>(a, g.count, cl, smem, stream);
+    return launch_sweep<T, C, 256, kSweepNPT>(a, g.count, cl, smem, stream);
 }
 
-cudaError_t sweep_launch_any(lb_handle* h, int var, int nt, int cl, int n_clusters, double tol, int check,
-                             long long max_steps) {
+cudaError_t sweep_launch_any(lb_handle* h, const SweepGroup& g, int var, int nt, int cl, double tol, int check,
+                             long long max_steps, cudaStream_t stream) {
     return with_types(h->prec, [&](auto tt, auto tc) -> cudaError_t {
         LB_TYPES(tt, tc);
         if constexpr (std::is_same<T, double>::value != std::is_same<C, double>::value) return cudaErrorNotSupported;
-        else return sweep_launch<T, C>(h, var, nt, cl, n_clusters, tol, check, max_steps);
+        else return sweep_launch<T, C>(h, g, var, nt, cl, tol, check, max_steps, stream);
     });
 }
 
-// Stable channels, widest first (the longest-running clusters start first).
+// Stable channels, widest first (the longest-running clusters start first), split into width
+// classes; a class keeps the configuration it was tuned (or set) with.
 lb_status sweep_order(lb_handle* h, int* n_active) {
     std::vector<int> st(h->n_ch);
     LB_CK(cudaMemcpyAsync(st.data(), h->status_d, sizeof(int) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
@@ -863,21 +877,32 @@ lb_status sweep_order(lb_handle* h, int* n_active) {
     }
     if (!order.empty())
         LB_CK(cudaMemcpy(h->sweep_order_d, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
+    std::vector<SweepGroup> groups;
+    for (int k = 0; k < (int)order.size(); ++k) {
+        const int ny = h->ny[order[k]];
+        if (groups.empty() || width_class(ny) != groups.back().cls) {
+            SweepGroup g;
+            g.cls = width_class(ny);
+            g.begin = k;
+            g.ny_max = ny;
+            for (const SweepGroup& old : h->sweep_groups)
+                if (old.cls == g.cls) { g.var = old.var; g.nt = old.nt; g.cl = old.cl; g.tune_ms = old.tune_ms; }
+            groups.push_back(g);
+        }
+        groups.back().count += 1;
+        groups.back().ny_min = ny;
+    }
+    for (SweepGroup& g : groups)  // a kept configuration must still fit (it does when channels only retire)
+        if (g.nt && !sweep_config_fits(h, g, g.var, g.nt, g.cl)) g.nt = 0;
+    h->sweep_groups = groups;
     *n_active = (int)order.size();
     return LB_OK;
 }
 
-// Autotuner: time a short sweep (no channel can converge: tol < 0) for every (threads, cluster
-// size) that fits, from the same saved state, and keep the fastest.  The state is restored.
-lb_status sweep_tune(lb_handle* h, int n_active) {
-    struct Cand { int var, nt, cl; };
-    std::vector<Cand> cands;
-    for (int nt : {128, 256})
-        for (int cl : {1, 2, 4, 8, 16}) {
-            if (sweep_fits(h, nt, cl) && sweep_smem(h, cl) <= 200 * 1024) cands.push_back({0, nt, cl});
-            if (sweep_smem_fits(h, nt, cl)) cands.push_back({1, nt, cl});
-        }
-    if (cands.empty()) return fail(LB_EINVAL, "lb_run_until_steady: a channel is too wide for the sweep kernel%s");
+// Autotuner: per width class, time a short sweep of that class alone (no channel can converge:
+// tol < 0) for every (kernel, threads, cluster size) that fits, from the same saved state, and
+// keep the fastest.  The state is restored.
+lb_status sweep_tune(lb_handle* h, bool all) {
     const size_t pop_b = 9 * h->planes * h->tsize, dr_b = h->planes * h->csize, up_b = 2 * h->planes * h->csize;
     void* save = nullptr;
     LB_CK(cudaMalloc(&save, pop_b + dr_b + up_b));
@@ -894,42 +919,81 @@ lb_status sweep_tune(lb_handle* h, int n_active) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    double best = 1e300;
-    for (const Cand& c : cands) {
+    bool none = false;
+    for (SweepGroup& g : h->sweep_groups) {
         if (e != cudaSuccess) break;
-        float ms = 0.f;
-        bool launched = true;
-        for (int rep = 0; rep < 2 && e == cudaSuccess && launched; ++rep) {  // first run warms up
-            e = restore();
-            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-            if (e == cudaSuccess) {
-                // a cluster shape the device cannot co-schedule is refused at launch (a
-                // configuration error that leaves the context usable): skip the candidate
-                const cudaError_t le = sweep_launch_any(h, c.var, c.nt, c.cl, n_active, -1.0, 16, 256);
-                if (le != cudaSuccess) {
-                    launched = false;
-                    (void)cudaGetLastError();
+        if (g.nt && !all) continue;
+        double best = 1e300;
+        for (int var : {0, 1})
+            for (int nt : {128, 256})
+                for (int cl : {1, 2, 4, 8, 16}) {
+                    if (e != cudaSuccess || !sweep_config_fits(h, g, var, nt, cl)) continue;
+                    float ms = 0.f;
+                    bool launched = true;
+                    for (int rep = 0; rep < 2 && e == cudaSuccess && launched; ++rep) {  // first run warms up
+                        e = restore();
+                        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+                        if (e == cudaSuccess) {
+                            // a cluster shape the device cannot co-schedule is refused at launch (a
+                            // configuration error that leaves the context usable): skip it
+                            const cudaError_t le = sweep_launch_any(h, g, var, nt, cl, -1.0, 16, 256, h->stream);
+                            if (le != cudaSuccess) {
+                                launched = false;
+                                (void)cudaGetLastError();
+                            }
+                        }
+                        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    }
+                    if (e == cudaSuccess && launched && ms < best) {
+                        best = ms;
+                        g.var = var;
+                        g.nt = nt;
+                        g.cl = cl;
+                        g.tune_ms = ms;
+                    }
                 }
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        }
-        if (e == cudaSuccess && launched && ms < best) {
-            best = ms;
-            h->sweep_nt = c.nt;
-            h->sweep_cl = c.cl;
-            h->sweep_var = c.var;
-        }
+        if (best == 1e300) none = true;
     }
     if (e == cudaSuccess) e = restore();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(save);
-    if (e != cudaSuccess) { h->sweep_nt = h->sweep_cl = 0; return cuda_fail(e, "lb_run_until_steady: autotune"); }
-    if (best == 1e300) { h->sweep_nt = h->sweep_cl = 0; return fail(LB_ECUDA, "lb_run_until_steady: no sweep configuration could be launched%s"); }
-    h->sweep_tune_ms = best;
+    if (e != cudaSuccess || none) {
+        for (SweepGroup& g : h->sweep_groups) g.nt = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "lb_run_until_steady: autotune");
+        return fail(LB_ECUDA, "lb_run_until_steady: a channel is too wide for the sweep kernels, or no configuration could be launched%s");
+    }
+    return LB_OK;
+}
+
+// One persistent launch per width class on forked streams, joined back into the handle's stream.
+lb_status sweep_run(lb_handle* h, double tol, int check, long long max_steps) {
+    const size_t G = h->sweep_groups.size();
+    if (G == 1) {
+        const SweepGroup& g = h->sweep_groups[0];
+        LB_CK(sweep_launch_any(h, g, g.var, g.nt, g.cl, tol, check, max_steps, h->stream));
+        return LB_OK;
+    }
+    if (!h->fork_ev) LB_CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    while (h->gstreams.size() < G) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        LB_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        h->gstreams.push_back(s);
+        LB_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        h->gevents.push_back(ev);
+    }
+    LB_CK(cudaEventRecord(h->fork_ev, h->stream));
+    for (size_t k = 0; k < G; ++k) {
+        const SweepGroup& g = h->sweep_groups[k];
+        LB_CK(cudaStreamWaitEvent(h->gstreams[k], h->fork_ev, 0));
+        LB_CK(sweep_launch_any(h, g, g.var, g.nt, g.cl, tol, check, max_steps, h->gstreams[k]));
+        LB_CK(cudaEventRecord(h->gevents[k], h->gstreams[k]));
+    }
+    for (size_t k = 0; k < G; ++k) LB_CK(cudaStreamWaitEvent(h->stream, h->gevents[k], 0));
     return LB_OK;
 }
 
@@ -955,13 +1019,16 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
     std::vector<long long> steps(h->n_ch, 0);
     std::vector<double> res(h->n_ch, NAN);
     if (n_active > 0) {
-        if (!h->sweep_nt) {
-            st = sweep_tune(h, n_active);
+        bool untuned = false;
+        for (const SweepGroup& g : h->sweep_groups) untuned |= g.nt == 0;
+        if (untuned) {
+            st = sweep_tune(h, false);
             if (st != LB_OK) return st;
         }
         std::vector<long long> init(h->n_ch, -3);
         LB_CK(cudaMemcpy(h->sweep_steps_d, init.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice));
-        LB_CK(sweep_launch_any(h, h->sweep_var, h->sweep_nt, h->sweep_cl, n_active, tol, (int)check_every, ms));
+        st = sweep_run(h, tol, (int)check_every, ms);
+        if (st != LB_OK) return st;
         LB_CK(cudaMemcpyAsync(steps.data(), h->sweep_steps_d, sizeof(long long) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
         LB_CK(cudaMemcpyAsync(res.data(), h->sweep_res_d, sizeof(double) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
         LB_CK(cudaStreamSynchronize(h->stream));
@@ -983,29 +1050,56 @@ lb_status lb_sweep_tune(lb_handle* h) {
     int n_active = 0;
     lb_status st = sweep_order(h, &n_active);
     if (st != LB_OK || n_active == 0) return st;
-    return sweep_tune(h, n_active);
+    return sweep_tune(h, true);
 }
 
-int lb_sweep_variant(const lb_handle* h) { return h ? h->sweep_var : -1; }
+int lb_sweep_variant(const lb_handle* h) {
+    if (!h || h->sweep_groups.empty()) return -1;
+    return h->sweep_groups[0].var;
+}
+
+int lb_sweep_groups(const lb_handle* h, int* variant, int* threads, int* cluster, int* channels, int max_groups) {
+    if (!h) return -1;
+    const int G = (int)h->sweep_groups.size();
+    for (int k = 0; k < G && k < max_groups; ++k) {
+        const SweepGroup& g = h->sweep_groups[k];
+        if (variant) variant[k] = g.var;
+        if (threads) threads[k] = g.nt;
+        if (cluster) cluster[k] = g.cl;
+        if (channels) channels[k] = g.count;
+    }
+    return G;
+}
 
 lb_status lb_sweep_set_config(lb_handle* h, int variant, int threads, int cluster) {
     if (!h || (variant != 0 && variant != 1) || (threads != 128 && threads != 256))
         return fail(LB_EINVAL, "lb_sweep_set_config: variant 0/1 and threads 128/256%s");
-    const bool ok = variant == 0 ? (sweep_fits(h, threads, cluster) && sweep_smem(h, cluster) <= 200 * 1024)
-                                 : sweep_smem_fits(h, threads, cluster);
-    if (cluster < 1 || cluster > 16 || !ok) return fail(LB_EINVAL, "lb_sweep_set_config: configuration does not fit these channels%s");
-    h->sweep_var = variant;
-    h->sweep_nt = threads;
-    h->sweep_cl = cluster;
-    h->sweep_tune_ms = 0.0;
+    if (h->smode != 0 || h->gpbc || h->moving) return fail(LB_EINVAL, "lb_sweep_set_config: not a sweep handle%s");
+    int n_active = 0;
+    lb_status st = sweep_order(h, &n_active);
+    if (st != LB_OK) return st;
+    for (const SweepGroup& g : h->sweep_groups)
+        if (!sweep_config_fits(h, g, variant, threads, cluster))
+            return fail(LB_EINVAL, "lb_sweep_set_config: configuration does not fit these channels%s");
+    for (SweepGroup& g : h->sweep_groups) {
+        g.var = variant;
+        g.nt = threads;
+        g.cl = cluster;
+        g.tune_ms = 0.0;
+    }
     return LB_OK;
 }
 
 lb_status lb_sweep_config(lb_handle* h, int* threads, int* cluster, double* tune_ms) {
     if (!h) return fail(LB_EINVAL, "lb_sweep_config: null handle%s");
-    if (threads) *threads = h->sweep_nt;
-    if (cluster) *cluster = h->sweep_cl;
-    if (tune_ms) *tune_ms = h->sweep_tune_ms;
+    const SweepGroup* g = h->sweep_groups.empty() ? nullptr : &h->sweep_groups[0];
+    if (threads) *threads = g ? g->nt : 0;
+    if (cluster) *cluster = g ? g->cl : 0;
+    if (tune_ms) {
+        double t = 0.0;
+        for (const SweepGroup& q : h->sweep_groups) t += q.tune_ms;
+        *tune_ms = t;
+    }
     return LB_OK;
 }
 

@@ -93,6 +93,7 @@ def load():
         "lb_run_until_steady": ([_H, c_double, c_long, c_long, c_void_p, c_void_p], c_int),
         "lb_sweep_config": ([_H, POINTER(c_int), POINTER(c_int), POINTER(c_double)], c_int),
         "lb_sweep_variant": ([_H], c_int),
+        "lb_sweep_groups": ([_H, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int), c_int], c_int),
         "lb_sweep_set_config": ([_H, c_int, c_int, c_int], c_int),
         "lb_sweep_tune": ([_H], c_int),
         "lb_field_monitor_static": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p], c_int),
@@ -250,6 +251,16 @@ def lb_sweep_config(h: int):
 
 def lb_sweep_variant(h: int) -> int:
     return int(load().lb_sweep_variant(h))
+
+
+def lb_sweep_groups(h: int):
+    """[(kernel variant, threads, cluster, channels)] per width class of the sweep."""
+    n = int(load().lb_sweep_groups(h, None, None, None, None, 0))
+    if n <= 0:
+        return []
+    v, t, c, k = (c_int * n)(), (c_int * n)(), (c_int * n)(), (c_int * n)()
+    load().lb_sweep_groups(h, v, t, c, k, n)
+    return [(v[i], t[i], c[i], k[i]) for i in range(n)]
 
 
 def lb_sweep_set_config(h: int, variant: int, threads: int, cluster: int):
