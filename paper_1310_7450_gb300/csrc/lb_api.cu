@@ -342,6 +342,8 @@ struct lb_handle {
     std::vector<cudaStream_t> gstreams;     // forked streams of the class launches
     std::vector<cudaEvent_t> gevents;
     cudaEvent_t fork_ev = nullptr;
+    cudaGraphExec_t sweep_gexec = nullptr;  // the class launches captured as one graph ...
+    std::vector<double> sweep_key;          // ... for these arguments and configurations
     MarchItem* march_items_d = nullptr;
     int* march_item_begin_d = nullptr;  // {0, n_march_items}: the residual reduction's item range
     int n_march_items = 0, march_grid = 0;
@@ -577,6 +579,7 @@ void release(lb_handle* h) {
     for (cudaStream_t q : h->gstreams) cudaStreamDestroy(q);
     for (cudaEvent_t q : h->gevents) cudaEventDestroy(q);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->sweep_gexec) cudaGraphExecDestroy(h->sweep_gexec);
     delete h;
 }
 
@@ -969,31 +972,53 @@ lb_status sweep_tune(lb_handle* h, bool all) {
     return LB_OK;
 }
 
-// One persistent launch per width class on forked streams, joined back into the handle's stream.
+// One persistent launch per width class on forked streams, joined back: captured once as a CUDA
+// graph (on the handle's private capture stream) and replayed while the arguments and the class
+// configurations stay the same.
 lb_status sweep_run(lb_handle* h, double tol, int check, long long max_steps) {
     const size_t G = h->sweep_groups.size();
-    if (G == 1) {
-        const SweepGroup& g = h->sweep_groups[0];
-        LB_CK(sweep_launch_any(h, g, g.var, g.nt, g.cl, tol, check, max_steps, h->stream));
-        return LB_OK;
+    const uint32_t key_sr = step_key(h, h->step + 0x5bd1e995ll);
+    std::vector<double> key = {tol, (double)check, (double)max_steps, (double)key_sr};
+    for (const SweepGroup& g : h->sweep_groups)
+        for (int v : {g.begin, g.count, g.ny_min, g.ny_max, g.var, g.nt, g.cl}) key.push_back((double)v);
+    if (!h->sweep_gexec || key != h->sweep_key) {
+        if (h->sweep_gexec) {
+            LB_CK(cudaGraphExecDestroy(h->sweep_gexec));
+            h->sweep_gexec = nullptr;
+        }
+        if (!h->cap_stream) LB_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        if (!h->fork_ev) LB_CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        while (h->gstreams.size() < G) {
+            cudaStream_t q = nullptr;
+            cudaEvent_t ev = nullptr;
+            LB_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+            h->gstreams.push_back(q);
+            LB_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            h->gevents.push_back(ev);
+        }
+        cudaStream_t cap = h->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "lb_run_until_steady: graph capture begin");
+        e = cudaEventRecord(h->fork_ev, cap);
+        for (size_t k = 0; k < G && e == cudaSuccess; ++k) {
+            const SweepGroup& g = h->sweep_groups[k];
+            e = cudaStreamWaitEvent(h->gstreams[k], h->fork_ev, 0);
+            if (e == cudaSuccess) e = sweep_launch_any(h, g, g.var, g.nt, g.cl, tol, check, max_steps, h->gstreams[k]);
+            if (e == cudaSuccess) e = cudaEventRecord(h->gevents[k], h->gstreams[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, h->gevents[k], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->sweep_gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            h->sweep_gexec = nullptr;
+            return cuda_fail(e, "lb_run_until_steady: graph capture");
+        }
+        h->sweep_key = key;
     }
-    if (!h->fork_ev) LB_CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
-    while (h->gstreams.size() < G) {
-        cudaStream_t s = nullptr;
-        cudaEvent_t ev = nullptr;
-        LB_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-        h->gstreams.push_back(s);
-        LB_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        h->gevents.push_back(ev);
-    }
-    LB_CK(cudaEventRecord(h->fork_ev, h->stream));
-    for (size_t k = 0; k < G; ++k) {
-        const SweepGroup& g = h->sweep_groups[k];
-        LB_CK(cudaStreamWaitEvent(h->gstreams[k], h->fork_ev, 0));
-        LB_CK(sweep_launch_any(h, g, g.var, g.nt, g.cl, tol, check, max_steps, h->gstreams[k]));
-        LB_CK(cudaEventRecord(h->gevents[k], h->gstreams[k]));
-    }
-    for (size_t k = 0; k < G; ++k) LB_CK(cudaStreamWaitEvent(h->stream, h->gevents[k], 0));
+    LB_CK(cudaGraphLaunch(h->sweep_gexec, h->stream));
     return LB_OK;
 }
 

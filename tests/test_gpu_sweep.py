@@ -171,3 +171,19 @@ def test_shared_memory_sweep_converges_and_retires(stream):
         status = sim.status()
     assert steps[0] == -1 and steps[1] == -2
     assert list(status) == [0, 1]
+
+
+def test_sweep_graph_replayed_across_calls(stream):
+    """Width classes run as one captured graph of per-class persistent launches; a second call with
+    the same arguments replays it.  Two calls of 200 steps equal one call of 400 steps."""
+    nys = [9, 24, 80, 130]
+    ps = channel_set(nys, 90)
+    with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as a, lbnlm.Channels(4, nys, ps, "f64", stream=stream) as b:
+        assert len(lbnlm.lb_sweep_groups(a.h)) == 0
+        a.run_until_steady(-1.0, check_every=10, max_steps=200)
+        assert len(lbnlm.lb_sweep_groups(a.h)) == 4          # classes 3, 4, 6, 7
+        a.run_until_steady(-1.0, check_every=10, max_steps=200)
+        b.run_until_steady(-1.0, check_every=10, max_steps=400)
+        pa, pb = a.populations(), b.populations()
+    for k in range(len(nys)):
+        assert rel(pa[k][0], pb[k][0]) < 1e-14
