@@ -193,13 +193,18 @@ lb_status lb_channel_status(lb_handle *h, int *status);
  * ||u(t) - u(t-k)|| / (k ||u(t)||), is <= tol, checked every k = check_every steps (even, >= 2), or
  * until max_steps (rounded up to a multiple of k).  Over one step that change sits on the FP32
  * rounding floor of a steady state; over k steps the floor falls as 1/k while a smooth exponential
- * approach to the steady state gives the one-step value.  ONE persistent launch: each channel is owned by a thread-block cluster that runs
- * its own time loop (hardware cluster barrier per step) and leaves when the channel has converged;
- * the widest channels start first.  The first call tunes the CTA size and the cluster size by timing
- * short sweeps from the current state (the state is restored) -- see lb_sweep_config.  Outputs
- * (host, [n_channels], may be NULL): steps taken (-1: max_steps reached, -2: unstable) and the last
- * residual.  Each channel advances by its own number of steps; lb_step_count() is not changed.
- * Stress mode 0 only.  Synchronises the stream. */
+ * approach to the steady state gives the one-step value.  Each channel is owned by a
+ * thread-block cluster that runs its own time loop (hardware cluster barrier per step) and leaves
+ * when the channel has converged; the channels run as width classes, one persistent launch per
+ * class, the class launches captured as one CUDA graph (see lb_sweep_groups).  The run proceeds in
+ * segments of 64, 256, 1024, ... check intervals: after each, converged channels drop out and a
+ * class that lost half of its channels is tuned again (the slowest channels then run with the
+ * shape of lowest per-step latency); a channel's first check interval in a segment only saves its
+ * velocity.  The first call tunes each class by timing short sweeps from the current state (the
+ * state is restored).  Outputs (host, [n_channels], may be NULL): steps taken (-1: max_steps
+ * reached, -2: unstable) and the last residual.  Each channel advances by its own number of
+ * steps; lb_step_count() is not changed.  Stress mode 0, periodic x, bounce-back walls only.
+ * Synchronises the stream. */
 lb_status lb_run_until_steady(lb_handle *h, double tol, long check_every, long max_steps, long long *steps_out,
                               double *residual_out);
 /* Run the sweep autotuner now (otherwise the first lb_run_until_steady does); the state is kept. */

@@ -342,6 +342,7 @@ struct lb_handle {
     std::vector<cudaStream_t> gstreams;     // forked streams of the class launches
     std::vector<cudaEvent_t> gevents;
     cudaEvent_t fork_ev = nullptr;
+    bool sweep_fixed = false;               // configuration set by lb_sweep_set_config
     cudaGraphExec_t sweep_gexec = nullptr;  // the class launches captured as one graph ...
     std::vector<double> sweep_key;          // ... for these arguments and configurations
     MarchItem* march_items_d = nullptr;
@@ -865,13 +866,13 @@ cudaError_t sweep_launch_any(lb_handle* h, const SweepGroup& g, int var, int nt,
 
 // Stable channels, widest first (the longest-running clusters start first), split into width
 // classes; a class keeps the configuration it was tuned (or set) with.
-lb_status sweep_order(lb_handle* h, int* n_active) {
+lb_status sweep_order(lb_handle* h, int* n_active, const std::vector<char>* only = nullptr) {
     std::vector<int> st(h->n_ch);
     LB_CK(cudaMemcpyAsync(st.data(), h->status_d, sizeof(int) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     std::vector<int> order;
     for (int c = 0; c < h->n_ch; ++c)
-        if (st[c] == 0) order.push_back(c);
+        if (st[c] == 0 && (!only || (*only)[c])) order.push_back(c);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->ny[a] > h->ny[b]; });
     if (!h->sweep_order_d) {
         LB_CK(cudaMalloc(&h->sweep_order_d, sizeof(int) * h->n_ch));
@@ -895,8 +896,14 @@ lb_status sweep_order(lb_handle* h, int* n_active) {
         groups.back().count += 1;
         groups.back().ny_min = ny;
     }
-    for (SweepGroup& g : groups)  // a kept configuration must still fit (it does when channels only retire)
+    for (SweepGroup& g : groups) {
+        // a kept configuration must still fit (it does when channels only leave); a class that has
+        // lost half of its channels is tuned again (few clusters: the timing becomes per-step
+        // latency instead of throughput), unless the configuration was fixed by the caller
         if (g.nt && !sweep_config_fits(h, g, g.var, g.nt, g.cl)) g.nt = 0;
+        for (const SweepGroup& old : h->sweep_groups)
+            if (old.cls == g.cls && g.nt && !h->sweep_fixed && 2 * g.count <= old.count) g.nt = 0;
+    }
     h->sweep_groups = groups;
     *n_active = (int)order.size();
     return LB_OK;
@@ -1037,29 +1044,60 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
         return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements periodic x and bounce-back walls only%s");
     if (h->prec == LB_PREC_F64S_F32M || h->prec == LB_PREC_F32S_F64M)
         return fail(LB_EINVAL, "lb_run_until_steady: diagnostic precision mixes are not supported%s");
-    int n_active = 0;
-    lb_status st = sweep_order(h, &n_active);
-    if (st != LB_OK) return st;
+    // Segments of growing length (64, 256, 1024, ... check intervals): after each one the
+    // converged channels drop out and the classes that lost half of their channels are tuned
+    // again, so the last, slowest channels run with the shape of lowest per-step latency.  A
+    // channel's first check interval in a segment only saves its velocity.
     const long long ms = (long long)((max_steps + check_every - 1) / check_every) * check_every;
-    std::vector<long long> steps(h->n_ch, 0);
+    std::vector<long long> total(h->n_ch, -3);   // -3: not run (unstable before)
     std::vector<double> res(h->n_ch, NAN);
-    if (n_active > 0) {
+    std::vector<char> active(h->n_ch, 1);
+    std::vector<long long> seg_steps(h->n_ch);
+    std::vector<double> seg_res(h->n_ch);
+    long long done = 0, seg = 64LL * check_every;
+    lb_status st = LB_OK;
+    bool first = true;
+    while (done < ms) {
+        int n_active = 0;
+        st = sweep_order(h, &n_active, &active);
+        if (st != LB_OK) return st;
+        if (n_active == 0) break;
         bool untuned = false;
         for (const SweepGroup& g : h->sweep_groups) untuned |= g.nt == 0;
         if (untuned) {
             st = sweep_tune(h, false);
             if (st != LB_OK) return st;
         }
+        const long long L = std::min(seg, ms - done);
         std::vector<long long> init(h->n_ch, -3);
         LB_CK(cudaMemcpy(h->sweep_steps_d, init.data(), sizeof(long long) * h->n_ch, cudaMemcpyHostToDevice));
-        st = sweep_run(h, tol, (int)check_every, ms);
+        st = sweep_run(h, tol, (int)check_every, L);
         if (st != LB_OK) return st;
-        LB_CK(cudaMemcpyAsync(steps.data(), h->sweep_steps_d, sizeof(long long) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
-        LB_CK(cudaMemcpyAsync(res.data(), h->sweep_res_d, sizeof(double) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
+        LB_CK(cudaMemcpyAsync(seg_steps.data(), h->sweep_steps_d, sizeof(long long) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
+        LB_CK(cudaMemcpyAsync(seg_res.data(), h->sweep_res_d, sizeof(double) * h->n_ch, cudaMemcpyDeviceToHost, h->stream));
         LB_CK(cudaStreamSynchronize(h->stream));
+        for (int c = 0; c < h->n_ch; ++c) {
+            if (!active[c] || seg_steps[c] == -3) {
+                if (first && active[c]) active[c] = 0;   // unstable before the sweep
+                continue;
+            }
+            res[c] = seg_res[c];
+            if (seg_steps[c] >= 0) {                     // converged in this segment
+                total[c] = done + seg_steps[c];
+                active[c] = 0;
+            } else if (seg_steps[c] == -2) {             // became unstable
+                total[c] = -2;
+                active[c] = 0;
+            } else {
+                total[c] = -1;
+            }
+        }
+        done += L;
+        seg *= 4;
+        first = false;
     }
     for (int c = 0; c < h->n_ch; ++c) {
-        if (steps_out) steps_out[c] = steps[c] == -3 ? -2 : steps[c];  // -3: not in the sweep (unstable before)
+        if (steps_out) steps_out[c] = total[c] == -3 ? -2 : total[c];
         if (residual_out) residual_out[c] = res[c];
     }
     h->uprev_state = -10;
@@ -1075,6 +1113,7 @@ lb_status lb_sweep_tune(lb_handle* h) {
     int n_active = 0;
     lb_status st = sweep_order(h, &n_active);
     if (st != LB_OK || n_active == 0) return st;
+    h->sweep_fixed = false;
     return sweep_tune(h, true);
 }
 
@@ -1112,6 +1151,7 @@ lb_status lb_sweep_set_config(lb_handle* h, int variant, int threads, int cluste
         g.cl = cluster;
         g.tune_ms = 0.0;
     }
+    h->sweep_fixed = true;
     return LB_OK;
 }
 
