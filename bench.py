@@ -387,10 +387,11 @@ def run_cessation(args):
 def run_sweep(args):
     """Batched sweep: the 512-channel draw (Nx = 4, Ny ~ U{32..1024}, g = b (32/Ny)^2 with
     b ~ logU[1e-8, 1e-5], theta = 10^(2 + 10 eps), eps ~ U[-0.1, 0.1], seed 3), FP32, all channels
-    from rest to a one-step residual <= tol in one persistent launch.  Baseline: the plain
-    per-channel scheme (one single-channel handle per channel, lb_step in chunks of `check` steps
-    and lb_residual between chunks); its time per step is measured on a stratified sample of
-    channels and multiplied by each channel's own step count (the same steps as in the sweep)."""
+    from rest to a check-interval residual <= tol (lb_run_until_steady: width classes, persistent
+    launches, one graph).  Baseline: the plain per-channel scheme (one single-channel handle per
+    channel, lb_step in chunks of `check` steps and lb_residual between chunks); its time per step
+    is measured on a stratified sample of channels and multiplied by each channel's own step count
+    (converged channels) or the cap (the others) -- the same steps as in the sweep."""
     import torch
     from paper_1310_7450_gb300 import build as libbuild
     from paper_1310_7450_gb300 import inputs, lbnlm
@@ -432,7 +433,9 @@ def run_sweep(args):
         one.close()
     xs = np.array([nys[c] for c in per_step]); ys = np.array([per_step[c] for c in per_step])
     fit = np.polyfit(xs, ys, 1)          # seconds per step as a function of Ny (launch-bound: ~flat)
-    est = float(sum(max(steps[c], 0) * np.polyval(fit, nys[c]) for c in range(len(nys))))
+    # the same work as the sweep: converged channels for their steps, the others up to the cap
+    cap = int(args.max_steps)
+    est = float(sum((steps[c] if steps[c] > 0 else cap) * np.polyval(fit, nys[c]) for c in range(len(nys))))
     line = {"metric": "batched-sweep time-to-steady (plain per-channel vs one persistent launch)",
             "value": wall, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": args.precision,
             "data": "synthetic", "config": {"workload": f"{len(nys)} channels, Nx=4, Ny~U{{32..1024}}, seed {args.sweep_seed}",
