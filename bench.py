@@ -394,14 +394,20 @@ def run_sweep(args):
     (converged channels) or the cap (the others) -- the same steps as in the sweep."""
     import torch
     from paper_1310_7450_gb300 import build as libbuild
-    from paper_1310_7450_gb300 import inputs, lbnlm
+    from paper_1310_7450_gb300 import inputs, lbnlm, replicas
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl")
     libbuild.build()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     params = inputs.sweep_channel_params(args.channels, args.sweep_seed)
     nys = [q.pop("ny") for q in params]
+    n_all = len(nys)
+    if ws > 1:  # independent channels: each rank runs its share, no collective on the data path
+        mine = replicas.partition_channels(nys, ws, rank)
+        nys, params = [nys[c] for c in mine], [params[c] for c in mine]
     sim = lbnlm.Channels(4, nys, params, args.precision, stream=stream.cuda_stream)
     t0 = time.perf_counter()
     lbnlm.lb_sweep_tune(sim.h)
@@ -436,6 +442,22 @@ def run_sweep(args):
     # the same work as the sweep: converged channels for their steps, the others up to the cap
     cap = int(args.max_steps)
     est = float(sum((steps[c] if steps[c] > 0 else cap) * np.polyval(fit, nys[c]) for c in range(len(nys))))
+    job = replicas.reduce_job({"wall": ("max", wall), "est": ("max", est), "converged": ("sum", int(conv.sum()))}, ws)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+        if rank != 0:
+            return 0
+        wall, est = job["wall"], job["est"]
+        line = {"metric": "batched-sweep time-to-steady (plain per-channel vs one persistent launch)",
+                "value": wall, "unit": "s", "higher_is_better": False, "n_gpus": ws, "scaling": "strong",
+                "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": f"{n_all} channels, Nx=4, Ny~U{{32..1024}}, seed {args.sweep_seed}, "
+                                       f"partitioned over {ws} GPUs", "tol": args.tol, "check_every": args.check,
+                           "max_steps": args.max_steps},
+                "converged": int(job["converged"]), "channels": n_all,
+                "baseline_plain_per_channel": {"estimated_s": est}, "speedup_vs_plain": est / wall if wall > 0 else None}
+        print(json.dumps(line), flush=True)
+        return 0
     line = {"metric": "batched-sweep time-to-steady (plain per-channel vs one persistent launch)",
             "value": wall, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": args.precision,
             "data": "synthetic", "config": {"workload": f"{len(nys)} channels, Nx=4, Ny~U{{32..1024}}, seed {args.sweep_seed}",
