@@ -595,7 +595,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-crop", type=int, default=256)
+    ap.add_argument("--ref-crop", type=int, default=512)
     ap.add_argument("--workload", default="channel", choices=["channel", "sweep", "warmstart", "cessation"])
     ap.add_argument("--train", type=int, default=20000)
     ap.add_argument("--train-seed", type=int, default=5)
