@@ -428,3 +428,43 @@ def test_graph_replay_equals_separate_launches_bitwise(stream, prec):
             assert np.array_equal(a, b)
     for m1, m2 in zip(g[2], ng[2]):
         assert np.array_equal(m1, m2)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_cessation_stopping_signature_on_gpu(stream, prec):
+    """The GPU reproduces the oracle's cessation of the yield-stress channel (theta = 100, 4 x 32,
+    steady state first): the mid-channel speed falls from 1 % to 0.01 % of its steady value in a
+    small fraction of the time it took to reach 1 % (finite-time stop, Sec. IV B), at the same
+    step counts as the oracle (+- one sampling interval)."""
+    from oracle import analytic
+    ny, nx, every = 32, 4, 500
+    p = inputs.yield_stress_channel(ny, theta=100.0, tau=1e4, wpH=0.5)
+    ua = analytic.channel_profile(ny, p["g_x"], p["G_inf"], p["tau0"], p["theta"], p["gamma_c"])
+
+    def times(advance, speed):
+        u0 = speed()
+        t, out = 0, {}
+        while t < 300000 and len(out) < 2:
+            advance(every)
+            t += every
+            um = speed()
+            for lv in (1e-2, 1e-4):
+                if lv not in out and um < lv * u0:
+                    out[lv] = t
+        return out
+
+    with lbnlm.Channels(nx, ny, p, prec, stream=stream) as sim:
+        u = np.zeros((ny, nx, 2))
+        u[..., 0] = ua[:, None]
+        lbnlm.lb_set_fields(sim.h, np.ascontiguousarray(u.reshape(-1)), np.ones(nx * ny))
+        sim.step(200000)
+        lbnlm.lb_set_body_force(sim.h, -1, 0.0)
+        tg = times(sim.step, lambda: sim.fields()[0][0][ny // 2, 0, 0])
+    st = oracle.flow_state(np.ones((ny, nx)), np.repeat(ua[:, None], nx, 1), np.zeros((ny, nx)), p["g_x"])
+    oracle.run(p, st, 200000)
+    pc = dict(p, g_x=0.0)
+    to = times(lambda n: oracle.run(pc, st, n), lambda: oracle.fields(pc, st)[0][ny // 2, 0, 0])
+    print(f"{prec}: GPU {tg}, oracle {to}")
+    assert (tg[1e-4] - tg[1e-2]) / tg[1e-2] <= 0.35
+    for lv in (1e-2, 1e-4):
+        assert abs(tg[lv] - to[lv]) <= every
