@@ -384,6 +384,30 @@ def run_cessation(args):
     return 0
 
 
+def plain_per_step(nys, params, args, stream):
+    """Seconds per step of the plain per-channel FP32 scheme (one single-channel handle, lb_step in
+    chunks of `check` steps with lb_residual between chunks), measured on a stratified sample of
+    the channels by width; returns the samples and a linear fit in Ny."""
+    import torch
+    from paper_1310_7450_gb300 import lbnlm
+    order = np.argsort(nys)
+    sample = order[np.linspace(0, len(order) - 1, args.baseline_sample).astype(int)]
+    per_step = {}
+    for c in sample:
+        one = lbnlm.Channels(4, nys[c], params[c], args.precision, stream=stream.cuda_stream)
+        one.step(args.check)
+        torch.cuda.synchronize()
+        n_chunks = max(2, args.baseline_steps // args.check)
+        t1 = time.perf_counter()
+        for _ in range(n_chunks):
+            one.step(args.check)
+            one.residual()
+        per_step[int(c)] = (time.perf_counter() - t1) / (n_chunks * args.check)
+        one.close()
+    xs = np.array([nys[c] for c in per_step]); ys = np.array([per_step[c] for c in per_step])
+    return per_step, np.polyfit(xs, ys, 1)
+
+
 def run_sweep(args):
     """Batched sweep: the 512-channel draw (Nx = 4, Ny ~ U{32..1024}, g = b (32/Ny)^2 with
     b ~ logU[1e-8, 1e-5], theta = 10^(2 + 10 eps), eps ~ U[-0.1, 0.1], seed 3), FP32, all channels
@@ -422,23 +446,7 @@ def run_sweep(args):
     wall = time.perf_counter() - t0
     sim.close()
     conv = steps > 0
-    # plain per-channel baseline on a stratified sample (by width)
-    order = np.argsort(nys)
-    sample = order[np.linspace(0, len(order) - 1, args.baseline_sample).astype(int)]
-    per_step = {}
-    for c in sample:
-        one = lbnlm.Channels(4, nys[c], params[c], args.precision, stream=stream.cuda_stream)
-        one.step(args.check)
-        torch.cuda.synchronize()
-        n_chunks = max(2, args.baseline_steps // args.check)
-        t1 = time.perf_counter()
-        for _ in range(n_chunks):
-            one.step(args.check)
-            one.residual()
-        per_step[int(c)] = (time.perf_counter() - t1) / (n_chunks * args.check)
-        one.close()
-    xs = np.array([nys[c] for c in per_step]); ys = np.array([per_step[c] for c in per_step])
-    fit = np.polyfit(xs, ys, 1)          # seconds per step as a function of Ny (launch-bound: ~flat)
+    per_step, fit = plain_per_step(nys, params, args, stream)
     # the same work as the sweep: converged channels for their steps, the others up to the cap
     cap = int(args.max_steps)
     est = float(sum((steps[c] if steps[c] > 0 else cap) * np.polyval(fit, nys[c]) for c in range(len(nys))))
@@ -548,6 +556,8 @@ def run_warmstart(args):
         st, r, wall, fl = steady(nys, ps, start)
         if name == "mlp_judged":
             wall += judge_s
+        if name == "rest":
+            st_rest = st
         res[name] = {"wall_s": wall, "converged": int((st > 0).sum()), "steps_sum": int(st[st > 0].sum()),
                      "steps_max": int(st.max()), "steps_median": float(np.median(st[st > 0])) if (st > 0).any() else None}
         if name == "analytic":
@@ -561,6 +571,16 @@ def run_warmstart(args):
             for key, a, b in (("u", prof[0], u_lb), ("sxy", prof[1], s_lb), ("N1", prof[2], n_lb)):
                 errs[key].append(float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)))
         return errs
+    # the plain per-channel FP32 scheme from rest on the same channels: its per-step time on a
+    # sample, times the steps each channel took from rest in the sweep (the cap where it did not
+    # converge, so this is a lower bound)
+    plain = None
+    if "rest" in res:
+        per_step, fit = plain_per_step(nys, ps, args, stream)
+        cap = int(args.max_steps)
+        est = float(sum((st_rest[c] if st_rest[c] > 0 else cap) * np.polyval(fit, nys[c]) for c in range(len(nys))))
+        plain = {"estimated_s_lower_bound": est, "per_step_us_by_ny": {str(nys[c]): round(1e6 * v, 2) for c, v in per_step.items()},
+                 "converged_within_cap": int((st_rest > 0).sum())}
     err_mlp = start_errors(rows)
     err_cf = start_errors(cf_rows)
     sur.close()
@@ -570,7 +590,7 @@ def run_warmstart(args):
                        "tol": args.tol, "check_every": args.check, "epochs": args.epochs},
             "train_data_sweep_s": wall_t, "train_s": train_s, "final_loss": losses[-1], "inference_s": infer_s,
             "judge_s": judge_s, "judge_picked_mlp": int((pick == 0).sum()),
-            "held_out": res,
+            "held_out": res, "plain_per_channel_from_rest": plain,
             "start_error_median": {"mlp": {k: float(np.median(v)) for k, v in err_mlp.items()},
                                    "closed_form": {k: float(np.median(v)) for k, v in err_cf.items()}},
             "start_error_p90": {"mlp": {k: float(np.percentile(v, 90)) for k, v in err_mlp.items()},
@@ -605,7 +625,7 @@ def main():
     ap.add_argument("--channels", type=int, default=512)
     ap.add_argument("--sweep-seed", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--check", type=int, default=100)
+    ap.add_argument("--check", type=int, default=1000)
     ap.add_argument("--max-steps", type=int, default=20_000_000)
     ap.add_argument("--baseline-sample", type=int, default=8)
     ap.add_argument("--baseline-steps", type=int, default=2000)
