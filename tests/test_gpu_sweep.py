@@ -187,3 +187,24 @@ def test_sweep_graph_replayed_across_calls(stream):
         pa, pb = a.populations(), b.populations()
     for k in range(len(nys)):
         assert rel(pa[k][0], pb[k][0]) < 1e-14
+
+
+def test_full_size_sweep_sampled_channels_match_oracle(stream):
+    """The 512-channel sweep draw (seed 3) in the benchmark's launch configuration (width classes,
+    tuned kernels, one graph), 2000 steps from rest: the narrowest, the widest and two middle
+    channels against the oracle (FP32: u within 1e-5, sigma within 5e-5)."""
+    ps = inputs.sweep_channel_params(512, 3)
+    nys = [q.pop("ny") for q in ps]
+    with lbnlm.Channels(4, nys, ps, "f32", stream=stream) as sim:
+        steps, _ = sim.run_until_steady(-1.0, check_every=1000, max_steps=2000)
+        assert np.all(steps == -1)
+        assert len(lbnlm.lb_sweep_groups(sim.h)) >= 5
+        fields = sim.fields()
+    order = np.argsort(nys)
+    for c in (order[0], order[170], order[340], order[-1]):
+        st = oracle.init_state(np.ones((nys[c], 4)))
+        oracle.run(ps[c], st, 2000, nthreads=8)
+        u_o, s_o, _ = oracle.fields(ps[c], st)
+        u_g, s_g, _ = fields[c]
+        print(f"ny {nys[c]}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e}")
+        assert rel(u_g, u_o) < 1e-5 and rel(s_g, s_o) < 5e-5
