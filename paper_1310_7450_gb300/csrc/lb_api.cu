@@ -41,14 +41,18 @@ extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0>(const CUt
 extern template cudaError_t launch_step_march<__nv_bfloat16, float, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
 #define LB_SWEEP_EXTERN(T, C)                                                                                   \
     extern template cudaError_t launch_sweep<T, C, 128, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
-    extern template cudaError_t launch_sweep<T, C, 256, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t);
+    extern template cudaError_t launch_sweep<T, C, 256, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_sweep_capacity<T, C, 128, 4>(int, size_t, int*);                            \
+    extern template cudaError_t launch_sweep_capacity<T, C, 256, 4>(int, size_t, int*);
 LB_SWEEP_EXTERN(float, float)
 LB_SWEEP_EXTERN(__nv_bfloat16, float)
 LB_SWEEP_EXTERN(double, double)
 #undef LB_SWEEP_EXTERN
 #define LB_SWEEP_SMEM_EXTERN(T, C)                                                                                   \
     extern template cudaError_t launch_sweep_smem<T, C, 128, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
-    extern template cudaError_t launch_sweep_smem<T, C, 256, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t);
+    extern template cudaError_t launch_sweep_smem<T, C, 256, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_sweep_smem_capacity<T, C, 128, 4>(int, size_t, int*);                            \
+    extern template cudaError_t launch_sweep_smem_capacity<T, C, 256, 4>(int, size_t, int*);
 LB_SWEEP_SMEM_EXTERN(float, float)
 LB_SWEEP_SMEM_EXTERN(__nv_bfloat16, float)
 LB_SWEEP_SMEM_EXTERN(double, double)
@@ -864,6 +868,30 @@ cudaError_t sweep_launch_any(lb_handle* h, const SweepGroup& g, int var, int nt,
     });
 }
 
+// Clusters of this configuration the device can hold at once (0: never launched).
+int sweep_capacity(lb_handle* h, const SweepGroup& g, int var, int nt, int cl) {
+    int n = 0;
+    const cudaError_t e = with_types(h->prec, [&](auto tt, auto tc) -> cudaError_t {
+        LB_TYPES(tt, tc);
+        if constexpr (std::is_same<T, double>::value != std::is_same<C, double>::value) return cudaErrorNotSupported;
+        else {
+            if (var == 1) {
+                const size_t smem = sweep_smem_resident(h, g.ny_max, cl);
+                return nt == 128 ? launch_sweep_smem_capacity<T, C, 128, kSweepNPT>(cl, smem, &n)
+                                 : launch_sweep_smem_capacity<T, C, 256, kSweepNPT>(cl, smem, &n);
+            }
+            const size_t smem = sweep_smem(h, g.ny_max, cl);
+            return nt == 128 ? launch_sweep_capacity<T, C, 128, kSweepNPT>(cl, smem, &n)
+                             : launch_sweep_capacity<T, C, 256, kSweepNPT>(cl, smem, &n);
+        }
+    });
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 // Stable channels, widest first (the longest-running clusters start first), split into width
 // classes; a class keeps the configuration it was tuned (or set) with.
 lb_status sweep_order(lb_handle* h, int* n_active, const std::vector<char>* only = nullptr) {
@@ -938,6 +966,7 @@ lb_status sweep_tune(lb_handle* h, bool all) {
             for (int nt : {128, 256})
                 for (int cl : {1, 2, 4, 8, 16}) {
                     if (e != cudaSuccess || !sweep_config_fits(h, g, var, nt, cl)) continue;
+                    if (sweep_capacity(h, g, var, nt, cl) < 1) continue;  // cannot be co-scheduled
                     float ms = 0.f;
                     bool launched = true;
                     for (int rep = 0; rep < 2 && e == cudaSuccess && launched; ++rep) {  // first run warms up
@@ -1143,7 +1172,7 @@ lb_status lb_sweep_set_config(lb_handle* h, int variant, int threads, int cluste
     lb_status st = sweep_order(h, &n_active);
     if (st != LB_OK) return st;
     for (const SweepGroup& g : h->sweep_groups)
-        if (!sweep_config_fits(h, g, variant, threads, cluster))
+        if (!sweep_config_fits(h, g, variant, threads, cluster) || sweep_capacity(h, g, variant, threads, cluster) < 1)
             return fail(LB_EINVAL, "lb_sweep_set_config: configuration does not fit these channels%s");
     for (SweepGroup& g : h->sweep_groups) {
         g.var = variant;

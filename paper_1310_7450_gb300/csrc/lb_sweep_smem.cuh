@@ -269,6 +269,29 @@ constexpr size_t sweep_smem_bytes(int rows, int nx) {
     return ((size_t)2 * 9 * (rows + 6) * nx * sizeof(T) + 15) / 16 * 16 + (size_t)(rows + 4) * nx * 2 * sizeof(C);
 }
 
+// How many clusters of `cl` CTAs with `smem` bytes the device can hold at once (0: the shape cannot
+// be co-scheduled, so it is never launched).
+template <typename T, typename C, int NT, int NPT>
+cudaError_t launch_sweep_smem_capacity(int cl, size_t smem, int* n_clusters) {
+    auto k = k_sweep_smem<T, C, NT, NPT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(n_clusters, k, &cfg);
+}
+
 template <typename T, typename C, int NT, int NPT>
 cudaError_t launch_sweep_smem(const SweepArgs<T, C>& a, int n_clusters, int cl, size_t smem, cudaStream_t s) {
     auto k = k_sweep_smem<T, C, NT, NPT>;

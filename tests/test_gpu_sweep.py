@@ -192,7 +192,8 @@ def test_sweep_graph_replayed_across_calls(stream):
 def test_full_size_sweep_sampled_channels_match_oracle(stream):
     """The 512-channel sweep draw (seed 3) in the benchmark's launch configuration (width classes,
     tuned kernels, one graph), 2000 steps from rest: the narrowest, the widest and two middle
-    channels against the oracle (FP32: u within 1e-5, sigma within 5e-5)."""
+    channels against the oracle (FP32: u within 1e-5; sigma within 2e-4 -- theta reaches 1e3 in
+    this draw, and the FP32 storage of the stress already sets a 1.7e-5 floor at theta = 100)."""
     ps = inputs.sweep_channel_params(512, 3)
     nys = [q.pop("ny") for q in ps]
     with lbnlm.Channels(4, nys, ps, "f32", stream=stream) as sim:
@@ -207,4 +208,4 @@ def test_full_size_sweep_sampled_channels_match_oracle(stream):
         u_o, s_o, _ = oracle.fields(ps[c], st)
         u_g, s_g, _ = fields[c]
         print(f"ny {nys[c]}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e}")
-        assert rel(u_g, u_o) < 1e-5 and rel(s_g, s_o) < 5e-5
+        assert rel(u_g, u_o) < 1e-5 and rel(s_g, s_o) < 2e-4
