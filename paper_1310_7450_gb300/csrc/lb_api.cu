@@ -1038,10 +1038,14 @@ lb_status sweep_run(lb_handle* h, double tol, int check, long long max_steps) {
         e = cudaEventRecord(h->fork_ev, cap);
         for (size_t k = 0; k < G && e == cudaSuccess; ++k) {
             const SweepGroup& g = h->sweep_groups[k];
-            e = cudaStreamWaitEvent(h->gstreams[k], h->fork_ev, 0);
-            if (e == cudaSuccess) e = sweep_launch_any(h, g, g.var, g.nt, g.cl, tol, check, max_steps, h->gstreams[k]);
-            if (e == cudaSuccess) e = cudaEventRecord(h->gevents[k], h->gstreams[k]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, h->gevents[k], 0);
+            e = cudaStreamWaitEvent(h->gstreams[k], h->fork_ev, 0);  // fork
+            if (e != cudaSuccess) break;
+            const cudaError_t el = sweep_launch_any(h, g, g.var, g.nt, g.cl, tol, check, max_steps, h->gstreams[k]);
+            // join the forked stream whatever the launch did, so that no stream stays in capture
+            e = cudaEventRecord(h->gevents[k], h->gstreams[k]);
+            const cudaError_t ej = cudaStreamWaitEvent(cap, h->gevents[k], 0);
+            if (e == cudaSuccess) e = ej;
+            if (e == cudaSuccess) e = el;
         }
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);

@@ -250,10 +250,9 @@ cudaError_t launch_sweep(const SweepArgs<T, C>& a, int n_clusters, int cl, size_
     auto k = k_sweep<T, C, NT, NPT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    // set every time: an earlier capacity query may have left a smaller limit
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_clusters * cl);
     cfg.blockDim = dim3(NT);
