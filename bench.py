@@ -205,10 +205,16 @@ def run_gpu(args):
     cfg, p = workload(args)
     nx, ny = cfg["nx"], cfg["ny"]
     flags = lbnlm.LB_GRID_STORE_SIGMA if args.store_sigma else 0
+    if args.tile_only:
+        flags |= lbnlm.LB_GRID_TILE_ONLY
     sim = lbnlm.Channels(nx, ny, p, args.precision, stress_mode=args.stress_mode, flags=flags,
-                         stream=stream.cuda_stream)
+                         stream=stream.cuda_stream, x_mode=args.x_mode, walls=args.walls)
+    if args.walls == "couette":
+        lbnlm.lb_set_wall_velocity(sim.h, -1, args.u_wall)
     nodes = nx * ny
     kernel = "k_step_march" if lbnlm.lb_uses_row_march(sim.h) else "k_step_tile"
+    # the tile kernel also launches one boundary-column kernel per step for pressure-driven ends
+    launches_per_step = 2 if (args.x_mode == "gpbc" and kernel == "k_step_tile") else 1
 
     def barrier():
         if ws > 1:
@@ -238,7 +244,7 @@ def run_gpu(args):
         t_max = float(tt.item())
     ms_step = t_max / args.steps
     value = ws * nodes / (ms_step * 1e-3) / 1e9
-    launches = args.steps + 1  # K fused step kernels + the residual reduction of the last step
+    launches = launches_per_step * args.steps + 1  # K fused steps (+ GPBC columns) + the residual reduction
 
     # end to end through the C ABI: per step the body force goes host -> device from pinned memory
     # (lb_set_body_force), one step runs, and the step's channel monitor (residual, flux, max |u|)
@@ -305,7 +311,10 @@ def run_gpu(args):
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision, "data": "synthetic",
             "config": {"workload": f"single large channel {nx}x{ny} start-up, nlM theta=100, gamma_c=0.1, "
-                                   f"tau_LB=0.9, g=1e-6, G_inf=1e-3; FP32 SoA deviations + 4-component stress",
+                                   f"tau_LB=0.9, g=1e-6, G_inf=1e-3; FP32 SoA deviations + 4-component stress"
+                                   + ("" if args.x_mode == "periodic" else "; pressure-driven ends (GPBC)")
+                                   + ("" if args.walls == "bounce_back" else f"; Couette wall u={args.u_wall:g}"),
+                       "x_mode": args.x_mode, "walls": args.walls, "kernel": kernel,
                        "nx": nx, "ny": ny, "precision": args.precision, "stress_mode": args.stress_mode,
                        "store_sigma": bool(args.store_sigma),
                        "l2": f"state {bpn * nodes / 2**30:.2f} GiB per step, larger than the 126 MB L2 (no flush)",
@@ -612,6 +621,10 @@ def main():
     ap.add_argument("--stress-mode", type=int, default=0)
     ap.add_argument("--no-store-sigma", dest="store_sigma", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--x-mode", default="periodic", choices=["periodic", "gpbc"])
+    ap.add_argument("--walls", default="bounce_back", choices=["bounce_back", "couette"])
+    ap.add_argument("--u-wall", type=float, default=0.01)
+    ap.add_argument("--tile-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
