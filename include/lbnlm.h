@@ -100,8 +100,9 @@ typedef struct {
  *                  p_+ - p_- = g_x (nx + 1), rho_+- = rho0 +- (3/2) g_x (nx + 1); there is no body
  *                  force and no flow-induced density (delta rho = 0, Eq. bodyforce keeps its first
  *                  line), and lb_create starts from the linear density between rho_+ and rho_- .
- *                  lb_set_body_force changes the pressure gradient.  Steps run on the general tile
- *                  kernel; lb_run_until_steady / lb_sweep_tune return LB_EINVAL. */
+ *                  lb_set_body_force changes the pressure gradient.  Wide single FP32/BF16 channels
+ *                  step on the row-march kernel's boundary variant, the others on the tile kernel;
+ *                  lb_run_until_steady / lb_sweep_tune return LB_EINVAL. */
 enum { LB_X_PERIODIC = 1, LB_X_GPBC = 2 };
 /* lb_boundary.walls:
  *   LB_WALLS_BOUNCE_BACK  half-way bounce-back walls at y = -1/2 and y = ny - 1/2 (Sec. II B).
@@ -109,7 +110,8 @@ enum { LB_X_PERIODIC = 1, LB_X_GPBC = 2 };
  *                         last row y = ny-1 lies on a wall moving with (u_wall, 0) whose incoming
  *                         populations follow Zou and He (gap ny - 1/2).  u_wall starts at 0 and is
  *                         set with lb_set_wall_velocity.  The prescribed velocity is that of the
- *                         wall row's populations, j / sum_i n_i.  Steps run on the general tile
+ *                         wall row's populations, j / sum_i n_i.  Wide single FP32/BF16 channels
+ *                         step on the row-march kernel's boundary variant, the others on the tile
  *                         kernel; lb_run_until_steady / lb_sweep_tune return LB_EINVAL. */
 enum { LB_WALLS_BOUNCE_BACK = 1, LB_WALLS_COUETTE = 2 };
 

@@ -61,6 +61,14 @@ extern template cudaError_t march_occupancy<float, float, 0>(int*);
 extern template cudaError_t march_occupancy<float, float, 1>(int*);
 extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0>(int*);
 extern template cudaError_t march_occupancy<__nv_bfloat16, float, 1>(int*);
+extern template cudaError_t launch_step_march<float, float, 0, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<float, float, 1, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<__nv_bfloat16, float, 1, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t march_occupancy<float, float, 0, 1>(int*);
+extern template cudaError_t march_occupancy<float, float, 1, 1>(int*);
+extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0, 1>(int*);
+extern template cudaError_t march_occupancy<__nv_bfloat16, float, 1, 1>(int*);
 }  // namespace lbk
 
 using namespace lbk;
@@ -484,7 +492,7 @@ bool make_pop_map(const lb_handle* h, void* base, CUtensorMap* map) {
 // work items fill one wave of resident CTAs.
 lb_status plan_march(lb_handle* h) {
     h->march = false;
-    if (h->gpbc || h->moving || h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
+    if (h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
         h->ny[0] < 16 || (h->flags & LB_GRID_TILE_ONLY))
         return LB_OK;
     if (!make_pop_map(h, h->popA, &h->mapA) || !make_pop_map(h, h->popB, &h->mapB)) return LB_OK;
@@ -493,8 +501,14 @@ lb_status plan_march(lb_handle* h) {
     int bps = 0, nsm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
     if (e == cudaSuccess) {
-        if (h->prec == LB_PREC_F32) e = h->smode ? march_occupancy<float, float, 1>(&bps) : march_occupancy<float, float, 0>(&bps);
-        else e = h->smode ? march_occupancy<__nv_bfloat16, float, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0>(&bps);
+        const bool bnd = h->gpbc || h->moving;
+        if (h->prec == LB_PREC_F32) {
+            if (bnd) e = h->smode ? march_occupancy<float, float, 1, 1>(&bps) : march_occupancy<float, float, 0, 1>(&bps);
+            else e = h->smode ? march_occupancy<float, float, 1>(&bps) : march_occupancy<float, float, 0>(&bps);
+        } else {
+            if (bnd) e = h->smode ? march_occupancy<__nv_bfloat16, float, 1, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0, 1>(&bps);
+            else e = h->smode ? march_occupancy<__nv_bfloat16, float, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0>(&bps);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "lb_create: march occupancy");
     if (bps < 1) return LB_OK;
@@ -664,6 +678,9 @@ template <>
 cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float>& a) {
     MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d};
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
+    if (h->gpbc || h->moving)
+        return h->smode ? launch_step_march<float, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
+                        : launch_step_march<float, float, 0, 1>(m, a, ctl, h->march_grid, h->stream);
     return h->smode ? launch_step_march<float, float, 1>(m, a, ctl, h->march_grid, h->stream)
                     : launch_step_march<float, float, 0>(m, a, ctl, h->march_grid, h->stream);
 }
@@ -671,6 +688,9 @@ template <>
 cudaError_t launch_march<__nv_bfloat16, float>(lb_handle* h, const StepArgs<__nv_bfloat16, float>& a) {
     MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d};
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
+    if (h->gpbc || h->moving)
+        return h->smode ? launch_step_march<__nv_bfloat16, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
+                        : launch_step_march<__nv_bfloat16, float, 0, 1>(m, a, ctl, h->march_grid, h->stream);
     return h->smode ? launch_step_march<__nv_bfloat16, float, 1>(m, a, ctl, h->march_grid, h->stream)
                     : launch_step_march<__nv_bfloat16, float, 0>(m, a, ctl, h->march_grid, h->stream);
 }
@@ -746,12 +766,9 @@ lb_status run_steps(lb_handle* h, long n) {
         if (s >= n - 1) f |= F_SAVE_U;
         if (resid) f |= F_RESID;
         a.flags = f;
-        if (h->march) {
-            LB_CK((launch_march<T, C>(h, a)));
-        } else {
-            LB_CK((gpbc_columns<T, C>(h)));
-            LB_CK((launch<T, C>(h, a)));
-        }
+        LB_CK((gpbc_columns<T, C>(h)));
+        if (h->march) LB_CK((launch_march<T, C>(h, a)));
+        else LB_CK((launch<T, C>(h, a)));
         if (resid) {
             k_reduce_residual<<<h->n_ch, kThreads, 0, h->stream>>>(h->partials, h->march ? h->march_item_begin_d : h->item_begin_d,
                                                                     h->status_d, h->mon_d, h->nx, h->step);

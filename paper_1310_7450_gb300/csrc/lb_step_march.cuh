@@ -97,7 +97,10 @@ constexpr size_t march_smem_bytes() {
     return 128 /*barriers*/ + K * slot + (size_t)4 * (W + 2) * 2 * sizeof(C);
 }
 
-template <typename T, typename C, int SMODE, int W, int K>
+// BND = 1: channel ends joined by the generalized periodic boundaries of Sec. II B and / or a
+// moving Couette wall on the last row (Sec. IV C), both applied where the populations are pulled
+// (the same rules as the tile kernel's pull9); BND = 0: periodic x and bounce-back walls only.
+template <typename T, typename C, int SMODE, int W, int K, int BND = 0>
 __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUtensorMap tmap, const StepArgs<T, C> a,
                                                   const MarchCtl ctl) {
     constexpr int HP = MarchGeom<T>::HP;
@@ -168,6 +171,16 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         auto patch_store = [&](int r, T v) {
             if (r >= 0 && r < ny && r <= rlast) const_cast<T*>(slot_ptr(idx_of(r)))[pi * SW + ps] = v;
         };
+        // boundary data of pressure-driven ends (BND = 1): the moments of the two end columns and
+        // the density shifts of the populations entering at x = 0 and at x = nx-1
+        const bool gp = BND == 1 && a.gcol != nullptr && P.gpbc != 0;
+        const C* gc = gp ? a.gcol + P.row_off : nullptr;
+        C dplus = C(0), dminus = C(0);
+        if (gp) {
+            const C* means = a.gcol + 6LL * a.gny;
+            dplus = P.rho_in - means[1];
+            dminus = P.rho_out - means[0];
+        }
         // pulled populations of node (col, r) from the slots (col relative to x0, may be -1 or W):
         // direction i comes from source row r - cy_i, column col - cx_i
         auto pull = [&](int col, int r, C (&d)[9]) {
@@ -191,6 +204,27 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                         d[i] = (C)Store<T>::cvt(sr[i * SW - cx(i)]);
                     }
                 }
+            }
+            if constexpr (BND == 1) {
+                if (gp && (left_edge || right_edge)) {
+                    // the node's true column; the slots hold the raw periodic images, so every
+                    // population that crosses an end gets its shift here (Sec. II B)
+                    const int xg = x0 + col;
+                    const int X = xg < 0 ? xg + nx : (xg >= nx ? xg - nx : xg);
+                    if (X == 0 || X == nx - 1) {
+#pragma unroll
+                        for (int i = 1; i < 9; ++i) {
+                            if (cx(i) == 0) continue;
+                            const int ys = r - cy(i);
+                            const int xr = X - cx(i);
+                            if (ys < 0 || ys >= ny || (xr >= 0 && xr < nx)) continue;
+                            const int c = xr < 0 ? 1 : 0;
+                            d[i] += gpbc_shift<C>(i, gc[c * a.gny + ys], gc[(2 + c) * a.gny + ys],
+                                                  gc[(4 + c) * a.gny + ys], xr < 0 ? dplus : dminus);
+                        }
+                    }
+                }
+                if (P.moving && r == ny - 1) zou_he_top<C>(d, P.u_wall);
             }
         };
         auto put_u = [&](int r, int col, C ux, C uy) {
@@ -412,10 +446,10 @@ namespace lbk {
 constexpr int kMarchW = 128;  // threads (= columns) per CTA
 constexpr int kMarchK = 8;    // shared-memory row slots (copies run K-2 rows ahead)
 
-template <typename T, typename C, int SMODE>
+template <typename T, typename C, int SMODE, int BND = 0>
 cudaError_t launch_step_march(const CUtensorMap& map, const StepArgs<T, C>& a, const MarchCtl& ctl, int grid,
                               cudaStream_t s) {
-    auto k = k_step_march<T, C, SMODE, kMarchW, kMarchK>;
+    auto k = k_step_march<T, C, SMODE, kMarchW, kMarchK, BND>;
     const size_t smem = march_smem_bytes<T, C, kMarchW, kMarchK>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -423,9 +457,9 @@ cudaError_t launch_step_march(const CUtensorMap& map, const StepArgs<T, C>& a, c
     return cudaGetLastError();
 }
 
-template <typename T, typename C, int SMODE>
+template <typename T, typename C, int SMODE, int BND = 0>
 cudaError_t march_occupancy(int* blocks_per_sm) {
-    auto k = k_step_march<T, C, SMODE, kMarchW, kMarchK>;
+    auto k = k_step_march<T, C, SMODE, kMarchW, kMarchK, BND>;
     const size_t smem = march_smem_bytes<T, C, kMarchW, kMarchK>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

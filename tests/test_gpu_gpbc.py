@@ -152,4 +152,41 @@ def test_gpbc_rejected_by_the_sweep(stream):
             sim.run_until_steady(1e-8, check_every=100, max_steps=1000)
         assert e.value.status == lbnlm.LB_EINVAL
     with lbnlm.Channels(4096, 64, nlm(), "f32", stream=stream, x_mode="gpbc") as wide:
-        assert not lbnlm.lb_uses_row_march(wide.h)
+        assert lbnlm.lb_uses_row_march(wide.h)          # wide single channels: the row march
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("nx", [128, 384])
+@pytest.mark.parametrize("x_mode,walls", [("gpbc", "bounce_back"), ("periodic", "couette"), ("gpbc", "couette")])
+def test_row_march_boundary_variant_matches_tile_kernel_and_oracle(stream, prec, nx, x_mode, walls):
+    """Wide single channels with pressure-driven ends and / or a moving wall run on the row-march
+    kernel's boundary variant (corrections applied where the populations are pulled, including
+    the halo columns of the edge strips; nx = 128 is a single strip that is both edges).  It must
+    agree with the tile kernel and, in FP32, with the oracle."""
+    ny = 48
+    p = dict(nlm(10.0, 2e-5), rho_pert_amp=1e-3, seed=5)
+    st = random_state(nx, ny, 77 + nx, amp=1e-3)
+    res = {}
+    for flags in (0, lbnlm.LB_GRID_TILE_ONLY):
+        with lbnlm.Channels(nx, ny, p, prec, flags=flags | lbnlm.LB_GRID_STORE_SIGMA, stream=stream,
+                            x_mode=x_mode, walls=walls) as sim:
+            assert lbnlm.lb_uses_row_march(sim.h) == (flags == 0)
+            if walls == "couette":
+                lbnlm.lb_set_wall_velocity(sim.h, -1, 0.01)
+            sim.set_populations([st.nstar], [st.drho])
+            sim.step(60)
+            (u, s, r), = sim.fields()
+            (n, d), = sim.populations()
+            res[flags] = (u, s, n)
+    u_m, s_m, n_m = res[0]
+    u_t, s_t, n_t = res[lbnlm.LB_GRID_TILE_ONLY]
+    w = oracle.WEIGHTS[:, None, None]
+    print(f"{prec} nx={nx} {x_mode}/{walls}: march vs tile u {rel(u_m, u_t):.2e}, populations {rel(n_m - w, n_t - w):.2e}")
+    if prec == "f32":
+        assert rel(u_m, u_t) < 1e-5 and rel(n_m - w, n_t - w) < 1e-5
+        po = dict(p, x_mode=x_mode, top_wall="moving" if walls == "couette" else "bounce_back", u_wall=0.01)
+        oracle.run(po, st, 60)
+        u_o, _, _ = oracle.fields(po, st)
+        assert rel(u_m, u_o) < 1e-4
+    else:
+        assert rel(u_m, u_t) < 1e-2
