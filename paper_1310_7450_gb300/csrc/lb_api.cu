@@ -515,19 +515,24 @@ lb_status plan_march(lb_handle* h) {
     const int strips = h->nx / kMarchW;
     const int slots = bps * nsm;
     // one wave: at most as many items as resident CTAs (a partial second wave would double the
-    // kernel time for a few CTAs)
-    int chunks = slots / strips;
+    // kernel time for a few CTAs).  With pressure-driven ends the two edge strips do extra work
+    // per row (the boundary-column shifts), so they get rows ranges half as long.
+    const bool split_edges = h->gpbc && strips > 1;
+    int chunks = slots / (strips + (split_edges ? 2 : 0));
     if (chunks > h->ny[0] / 8) chunks = h->ny[0] / 8;
     if (chunks < 1) chunks = 1;
+    const int echunks = split_edges ? std::max(chunks, std::min(2 * chunks, h->ny[0] / 8)) : chunks;
     std::vector<MarchItem> items;
-    for (int c = 0; c < chunks; ++c)
-        for (int s = 0; s < strips; ++s) {
+    for (int s = 0; s < strips; ++s) {
+        const int n = (s == 0 || s == strips - 1) ? echunks : chunks;
+        for (int c = 0; c < n; ++c) {
             MarchItem it{};
             it.x0 = s * kMarchW;
-            it.y0 = (int)((long long)h->ny[0] * c / chunks);
-            it.y1 = (int)((long long)h->ny[0] * (c + 1) / chunks);
+            it.y0 = (int)((long long)h->ny[0] * c / n);
+            it.y1 = (int)((long long)h->ny[0] * (c + 1) / n);
             items.push_back(it);
         }
+    }
     LB_CK(cudaMalloc(&h->march_items_d, sizeof(MarchItem) * items.size()));
     LB_CK(cudaMemcpy(h->march_items_d, items.data(), sizeof(MarchItem) * items.size(), cudaMemcpyHostToDevice));
     h->n_march_items = (int)items.size();

@@ -171,16 +171,6 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         auto patch_store = [&](int r, T v) {
             if (r >= 0 && r < ny && r <= rlast) const_cast<T*>(slot_ptr(idx_of(r)))[pi * SW + ps] = v;
         };
-        // boundary data of pressure-driven ends (BND = 1): the moments of the two end columns and
-        // the density shifts of the populations entering at x = 0 and at x = nx-1
-        const bool gp = BND == 1 && a.gcol != nullptr && P.gpbc != 0;
-        const C* gc = gp ? a.gcol + P.row_off : nullptr;
-        C dplus = C(0), dminus = C(0);
-        if (gp) {
-            const C* means = a.gcol + 6LL * a.gny;
-            dplus = P.rho_in - means[1];
-            dminus = P.rho_out - means[0];
-        }
         // pulled populations of node (col, r) from the slots (col relative to x0, may be -1 or W):
         // direction i comes from source row r - cy_i, column col - cx_i
         auto pull = [&](int col, int r, C (&d)[9]) {
@@ -206,12 +196,18 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                 }
             }
             if constexpr (BND == 1) {
-                if (gp && (left_edge || right_edge)) {
+                // (channel data are re-read here rather than kept live: only edge nodes and the
+                // wall row need them)
+                if ((left_edge || right_edge) && a.gcol != nullptr) {
                     // the node's true column; the slots hold the raw periodic images, so every
                     // population that crosses an end gets its shift here (Sec. II B)
                     const int xg = x0 + col;
                     const int X = xg < 0 ? xg + nx : (xg >= nx ? xg - nx : xg);
                     if (X == 0 || X == nx - 1) {
+                        const ChanParams<C>& Q = a.chan[0];
+                        const C* gc = a.gcol + Q.row_off;
+                        const C* means = a.gcol + 6LL * a.gny;
+                        const C dplus = Q.rho_in - means[1], dminus = Q.rho_out - means[0];
 #pragma unroll
                         for (int i = 1; i < 9; ++i) {
                             if (cx(i) == 0) continue;
@@ -224,7 +220,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                         }
                     }
                 }
-                if (P.moving && r == ny - 1) zou_he_top<C>(d, P.u_wall);
+                if (r == ny - 1 && a.chan[0].moving) zou_he_top<C>(d, a.chan[0].u_wall);
             }
         };
         auto put_u = [&](int r, int col, C ux, C uy) {
