@@ -369,6 +369,9 @@ struct lb_handle {
     // generalized periodic boundaries (x_mode LB_X_GPBC)
     bool gpbc = false;
     void* gcol = nullptr;  // boundary-column moments and means (see StepArgs::gcol)
+    double* gpart = nullptr;    // per-block partial sums of the column kernel
+    unsigned* gcount = nullptr; // per-column block counters (zero between launches)
+    int gpbc_max_ny = 0;
     int gny = 0;           // sum of ny over the channels
     std::vector<int> row_off;
     // planar Couette flow (walls LB_WALLS_COUETTE): Zou-He moving wall on the last row
@@ -593,6 +596,8 @@ void release(lb_handle* h) {
     free_dev(h->sweep_res_d);
     free_dev(h->sweep_order_d);
     free_dev(h->gcol);
+    free_dev(h->gpart);
+    free_dev(h->gcount);
     if (h->status_h) cudaFreeHost(h->status_h);
     if (h->gx_h) cudaFreeHost(h->gx_h);
     if (h->status_ev) cudaEventDestroy(h->status_ev);
@@ -666,7 +671,7 @@ template <typename T, typename C>
 cudaError_t gpbc_columns(lb_handle* h) {
     if (!h->gpbc) return cudaSuccess;
     return launch_gpbc_columns<T, C>((const T*)h->popA, (const ChanParams<C>*)h->chan, (C*)h->gcol, h->n_ch, h->nx,
-                                     h->gny, h->stream);
+                                     h->gny, h->gpbc_max_ny, h->gpart, h->gcount, h->stream);
 }
 
 template <typename T, typename C>
@@ -1302,7 +1307,13 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     LB_ALLOC(h->node_off_d, h->n_ch * sizeof(long long));
     LB_ALLOC(h->ny_d, h->n_ch * sizeof(int));
     LB_ALLOC(h->gx_d, 2 * h->n_ch * sizeof(double));
-    if (h->gpbc) LB_ALLOC(h->gcol, (6 * (size_t)h->gny + 2 * h->n_ch) * h->csize);
+    if (h->gpbc) {
+        for (int c = 0; c < h->n_ch; ++c) h->gpbc_max_ny = std::max(h->gpbc_max_ny, h->ny[c]);
+        const size_t rb = ((size_t)h->gpbc_max_ny + 255) / 256;
+        LB_ALLOC(h->gcol, (6 * (size_t)h->gny + 2 * h->n_ch) * h->csize);
+        LB_ALLOC(h->gpart, 2 * h->n_ch * rb * sizeof(double));
+        LB_ALLOC(h->gcount, 2 * h->n_ch * sizeof(unsigned));
+    }
 #undef LB_ALLOC
     e = cudaMallocHost((void**)&h->status_h, h->n_ch * sizeof(int));
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
@@ -1341,6 +1352,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     ok &= cudaMemcpy(h->ny_d, h->ny.data(), sizeof(int) * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(h->gx_d, gx.data(), sizeof(double) * 2 * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemsetAsync(h->status_d, 0, sizeof(int) * h->n_ch, h->stream) == cudaSuccess;
+    if (h->gcount) ok &= cudaMemsetAsync(h->gcount, 0, 2 * h->n_ch * sizeof(unsigned), h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(h->uprev, 0, 2 * h->planes * h->csize, h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(h->popB, 0, 9 * h->planes * h->tsize, h->stream) == cudaSuccess;
     if (h->sig4) ok &= cudaMemsetAsync(h->sig4, 0, 4 * h->planes * h->csize, h->stream) == cudaSuccess;

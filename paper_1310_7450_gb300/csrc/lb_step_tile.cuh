@@ -241,37 +241,56 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
 
 // GPBC boundary columns of the stored state: per node of the columns x = 0 and x = nx-1 the
 // density (as rho - 1) and momentum of its post-collision populations, and per column the mean
-// of rho - 1 (a fixed-order block reduction, so every step kernel sees the same value).  One CTA per
-// (channel, column); channels without GPBC are skipped.
+// of rho - 1.  One thread per row, RB blocks of NT rows per (channel, column); each block writes
+// its fixed-order partial sum, and the last block of a column to finish (a counter per column,
+// reset by that block) adds the partials in block order -- the same value every step kernel
+// sees, independent of the order in which blocks finish.  Channels without GPBC are skipped.
 template <typename T, typename C, int NT>
 __global__ void __launch_bounds__(NT) k_gpbc_columns(const T* __restrict__ pin, const ChanParams<C>* __restrict__ chan,
-                                                     C* __restrict__ gcol, int nx, int gny) {
-    const int ch = blockIdx.x >> 1, c = blockIdx.x & 1;
+                                                     C* __restrict__ gcol, int nx, int gny, int RB,
+                                                     double* __restrict__ gpart, unsigned* __restrict__ gcount) {
+    const int cc = blockIdx.x / RB, rb = blockIdx.x % RB;   // cc = 2 * channel + column
+    const int ch = cc >> 1, c = cc & 1;
     const ChanParams<C> P = chan[ch];
-    if (!P.gpbc) return;
+    const int nrb = (P.ny + NT - 1) / NT;
+    if (!P.gpbc || rb >= nrb) return;
     const int x = c ? nx - 1 : 0;
-    const T* pc = pin + 9 * P.base;
-    C* col = gcol + P.row_off;
-    double sum = 0.0;
-    for (int y = threadIdx.x; y < P.ny; y += NT) {
+    const int y = rb * NT + (int)threadIdx.x;
+    double v = 0.0;
+    if (y < P.ny) {
+        const T* pc = pin + 9 * P.base;
         C d[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) d[i] = Store<T>::ld(pc + (long long)i * P.P + (long long)y * nx + x);
         C dR, jx, jy;
         moments<C>(d, dR, jx, jy);
+        C* col = gcol + P.row_off;
         col[c * gny + y] = dR;
         col[(2 + c) * gny + y] = jx;
         col[(4 + c) * gny + y] = jy;
-        sum += (double)dR;
+        v = (double)dR;
     }
     __shared__ double red[NT];
-    red[threadIdx.x] = sum;
+    __shared__ bool last;
+    red[threadIdx.x] = v;
     __syncthreads();
     for (int h = NT / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) gcol[6LL * gny + 2 * ch + c] = (C)(red[0] / (double)P.ny);
+    if (threadIdx.x == 0) {
+        gpart[(long long)cc * RB + rb] = red[0];
+        __threadfence();
+        last = atomicAdd(gcount + cc, 1u) == (unsigned)(nrb - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double sum = 0.0;
+        for (int k = 0; k < nrb; ++k) sum += *(volatile double*)(gpart + (long long)cc * RB + k);
+        gcol[6LL * gny + cc] = (C)(sum / (double)P.ny);
+        gcount[cc] = 0u;
+    }
 }
 
 }  // namespace lbk
@@ -279,8 +298,10 @@ __global__ void __launch_bounds__(NT) k_gpbc_columns(const T* __restrict__ pin, 
 namespace lbk {
 template <typename T, typename C>
 cudaError_t launch_gpbc_columns(const T* pin, const ChanParams<C>* chan, C* gcol, int n_ch, int nx, int gny,
-                                cudaStream_t s) {
-    k_gpbc_columns<T, C, 256><<<2 * n_ch, 256, 0, s>>>(pin, chan, gcol, nx, gny);
+                                int max_ny, double* gpart, unsigned* gcount, cudaStream_t s) {
+    constexpr int NT = 256;
+    const int RB = (max_ny + NT - 1) / NT;
+    k_gpbc_columns<T, C, NT><<<2 * n_ch * RB, NT, 0, s>>>(pin, chan, gcol, nx, gny, RB, gpart, gcount);
     return cudaGetLastError();
 }
 
