@@ -686,7 +686,7 @@ template <typename T, typename C>
 cudaError_t launch_march(lb_handle*, const StepArgs<T, C>&) { return cudaErrorNotSupported; }
 template <>
 cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float>& a) {
-    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d};
+    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0]};
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
     if (h->gpbc || h->moving)
         return h->smode ? launch_step_march<float, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
@@ -696,7 +696,7 @@ cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float
 }
 template <>
 cudaError_t launch_march<__nv_bfloat16, float>(lb_handle* h, const StepArgs<__nv_bfloat16, float>& a) {
-    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d};
+    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0]};
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
     if (h->gpbc || h->moving)
         return h->smode ? launch_step_march<__nv_bfloat16, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)

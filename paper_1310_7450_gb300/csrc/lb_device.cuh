@@ -165,17 +165,29 @@ struct StepArgs {
 
 // ---- per-node arithmetic -------------------------------------------------------------------
 
-// Division and square root: exact IEEE operations in FP64 (the parity mode); in FP32 CUDA's fast
-// intrinsics (__fdividef and rsqrtf, 2 ulp) -- every denominator here is a density near 1 or a
-// positive quantity in the normal range, and the FP32 path's parity bound is 1e-5.
+// Division and square root: exact IEEE operations in FP64 (the parity mode); in FP32 the PTX
+// approximations rcp.approx.ftz and rsqrt.approx.ftz (one hardware instruction each, about 1 ulp;
+// the .ftz forms skip the subnormal handling) -- every denominator here is a density near 1 or a
+// positive quantity in the normal range, and the FP32 path's parity bound is 1e-5.  The square
+// root returns 0 below the smallest normal float: sqrt(x) < 1.1e-19 there, which no quantity it
+// enters (1 + tau sqrt(II)/gamma_c) can resolve.
 template <typename C> struct Arith;
 template <> struct Arith<double> {
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
 };
 template <> struct Arith<float> {
-    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-    static __device__ __forceinline__ float sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+    static __device__ __forceinline__ float rcp(float x) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
+    static __device__ __forceinline__ float sqrt(float x) {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return x >= 1.17549435e-38f ? x * r : 0.f;
+    }
 };
 
 // Moments of Eq. (rhoj) from the post-streaming deviations: dR = sum_i n_i - 1, J0 = sum c_i n_i.
@@ -265,9 +277,9 @@ __device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C k
     NodeState<C> r;
     const C Dxx = C(2) * ka, Dxy = kb + kc, Dyy = C(2) * ke;
     const C II = C(0.5) * (Dxx * Dxx + C(2) * Dxy * Dxy + Dyy * Dyy);  // (1/2) tr D^2
-    C tau_M = C(0);
-    if (P.tau > C(0)) tau_M = Arith<C>::div(P.tau, C(1) + P.tau * Arith<C>::sqrt(II) * P.inv_gc);
-    if (tau_M > C(0)) {
+    // tau = 0 (Newtonian) gives tau_M = 0, alpha = 0 and a zero right-hand side, so sigma = 0
+    const C tau_M = Arith<C>::div(P.tau, C(1) + P.tau * Arith<C>::sqrt(II) * P.inv_gc);
+    {
         if (SMODE == 0) {
             const C gt = P.G * tau_M;
             convected_solve<C>(ka, kb, kc, ke, tau_M, gt * Dxx, gt * Dxy, gt * Dyy, r.sxx, r.sxy, r.syy);
@@ -276,8 +288,6 @@ __device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C k
             convected_solve<C>(ka, kb, kc, ke, pre, pre * (s_old_xx + P.G * Dxx), pre * (s_old_xy + P.G * Dxy),
                                pre * (s_old_yy + P.G * Dyy), r.sxx, r.sxy, r.syy);
         }
-    } else {
-        r.sxx = r.sxy = r.syy = C(0);
     }
     const C Nxx = r.sxx + P.cD * Dxx;
     const C Nxy = r.sxy + P.cD * Dxy;

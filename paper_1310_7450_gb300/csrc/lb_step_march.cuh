@@ -12,7 +12,7 @@
 //      pulled from slots y, y+1, y+2 (Eq. lbupdate, pull form; bounce-back at the walls,
 //      Sec. II B); the own populations stay in registers for the next row's collision;
 //      the gradient velocity j/R0 goes into a 4-row ring in shared memory;
-//   2. barrier; one thread refills the slot of row y with row y+K;
+//   2. barrier; one thread (lane 0 of the last warp) refills the slot of row y with row y+K;
 //   3. collision of row y: kappa by three-point differences from the velocity ring, the nlM
 //      stress, Sigma^nN, delta rho, n^eq, F_i (Eq. bodyforce), BGK; coalesced stores.
 // The periodic wrap of x is patched into the halo columns of the first and last strip with
@@ -34,6 +34,8 @@ struct MarchCtl {
     const MarchItem* items;
     int n_items;
     int* timeout_flag;  // the channel status word: bit 2 is set when a bounded wait gave up
+    long long plane;    // plane stride of the channel's fields (elements)
+    long long base;     // plane offset of the channel (its planes start at k * base)
 };
 
 // ---- PTX helpers (mbarrier, TMA) ----------------------------------------------------------
@@ -121,6 +123,8 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
     if (a.status[0] != 0) return;
 
     __shared__ int s_bad;  // set by any thread whose bounded wait gave up; read after a barrier
+    constexpr int TI = W - 32;  // the thread that issues the copies (lane 0 of the last warp;
+                                // warp 0 computes the halo columns)
     if (t == 0) {
         s_bad = 0;
         prefetch_tmap(&tmap);
@@ -129,6 +133,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
     }
     __syncthreads();
 
+    bool vbad = false;  // some node of this CTA failed the velocity guard (reported when the CTA ends)
     uint32_t nload = 0;  // CTA-uniform count of copies issued (and, in order, consumed)
     bool bad = false;
 
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         const int pc = left_edge && t < 18 ? (nx - 2 + (t & 1)) : ((t - 32) & 1);     // global column
         const int ps = left_edge && t < 18 ? (HP - 2 + (t & 1)) : (HP + W + ((t - 32) & 1));  // slot column
         auto patch_load = [&](int r) -> T {
-            return (r >= 0 && r < ny && r <= rlast) ? a.pin[9 * P.base + (long long)pi * P.P + (long long)r * nx + pc] : T(0);
+            return (r >= 0 && r < ny && r <= rlast) ? a.pin[9 * ctl.base + (long long)pi * ctl.plane + (long long)r * nx + pc] : T(0);
         };
         auto patch_store = [&](int r, T v) {
             if (r >= 0 && r < ny && r <= rlast) const_cast<T*>(slot_ptr(idx_of(r)))[pi * SW + ps] = v;
@@ -235,8 +240,8 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                 pull(t, r, d);
                 gradient_velocity<C>(d, P.gx, dR, jx, jy, ux, uy);
                 put_u(r, t, ux, uy);
-                if (t == 32 || t == W - 32) {  // the two halo columns, on two different warps
-                    const int col = t == 32 ? -1 : W;
+                if (t < 2) {  // the two halo columns, on lanes 0 and 1 of one warp (one pass)
+                    const int col = t == 0 ? -1 : W;
                     C dh[9], hR, hx, hy;
                     pull(col, r, dh);
                     gradient_velocity<C>(dh, P.gx, hR, hx, hy, ux, uy);
@@ -248,7 +253,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         // ---- prologue: copies of rows rbase .. rbase+K-1; rows rbase .. rbase+5 waited and patched;
         // moments of rows y0-1, y0 (and of row 2 when the item starts at the bottom wall: the
         // one-sided difference of row 0 needs it)
-        if (t == 0) {
+        if (t == TI) {
             fence_proxy_async();
             for (int r = rbase; r < rbase + K && r <= rlast; ++r) issue(idx_of(r), x0, r);
         }
@@ -276,12 +281,12 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         }
         moments_row(y0, dcur, dRc, jxc, jyc);
         // the stored flow-induced density, loaded two rows ahead of its use
-        C drho_next = a.drho[P.base + (long long)y0 * nx + x];
-        C drho_next2 = (y0 + 1 < y1) ? a.drho[P.base + (long long)(y0 + 1) * nx + x] : C(0);
+        C drho_next = a.drho[ctl.base + (long long)y0 * nx + x];
+        C drho_next2 = (y0 + 1 < y1) ? a.drho[ctl.base + (long long)(y0 + 1) * nx + x] : C(0);
         // on residual steps the saved velocity of each row is prefetched the same way
         const bool resid = (a.flags & F_RESID) != 0;
-        const C* upx = a.uprev + 2 * P.base + x;
-        const C* upy = upx + P.P;
+        const C* upx = a.uprev + 2 * ctl.base + x;
+        const C* upy = upx + ctl.plane;
         C upx_next = C(0), upy_next = C(0), upx_next2 = C(0), upy_next2 = C(0);
         if (resid) {
             upx_next = upx[(long long)y0 * nx];
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             }
         }
         __syncthreads();
-        if (t == 0) {
+        if (t == TI) {
             fence_proxy_async();
             for (int r = rbase + K; r < rbase + K + 2 && r <= rlast; ++r) issue(idx_of(r), x0, r);
         }
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             moments_row(y + 1, dnext, dRn, jxn, jyn);
             const C drho_prev = drho_next;
             drho_next = drho_next2;
-            if (y + 2 < y1) drho_next2 = a.drho[P.base + (long long)(y + 2) * nx + x];
+            if (y + 2 < y1) drho_next2 = a.drho[ctl.base + (long long)(y + 2) * nx + x];
             const C upx_cur = upx_next, upy_cur = upy_next;
             if (resid) {
                 upx_next = upx_next2;
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             __syncthreads();
             if (s_bad) { bad = true; break; }
             // 2. refill the slot of row y (no longer read) with row y+K
-            if (t == 0 && y + K <= rlast) {
+            if (t == TI && y + K <= rlast) {
                 fence_proxy_async();
                 issue(idx_of(y + K), x0, y + K);
             }
@@ -350,36 +355,36 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                 C so_xx = 0, so_xy = 0, so_yy = 0;
                 const long long pn = (long long)y * nx + x;
                 if (SMODE == 1) {
-                    const C* s3 = a.sig3 + 3 * P.base;
+                    const C* s3 = a.sig3 + 3 * ctl.base;
                     so_xx = s3[pn];
-                    so_xy = s3[P.P + pn];
-                    so_yy = s3[2 * P.P + pn];
+                    so_xy = s3[ctl.plane + pn];
+                    so_yy = s3[2 * ctl.plane + pn];
                 }
                 const NodeState<C> s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dRc, jxc, jyc, drho_prev, so_xx, so_xy, so_yy);
                 const C rho_h = C(1) + s.dReq - s.drho;
-                if (!velocity_ok<C>(jxc, jyc, rho_h, a.guard)) atomicOr(a.status, 1);  // NaN or too fast
+                vbad |= !velocity_ok<C>(jxc, jyc, rho_h, a.guard);  // NaN or too fast
                 C D[9];
                 collide_node<C>(P, s, dcur, D);
-                T* po = a.pout + 9 * P.base + pn;
-                store_node<T, C>(po, P.P, dcur, D, (a.flags & F_SR) != 0, a.sr_key, (uint32_t)pn);
-                a.drho[P.base + pn] = s.drho;
+                T* po = a.pout + 9 * ctl.base + pn;
+                store_node<T, C>(po, ctl.plane, dcur, D, (a.flags & F_SR) != 0, a.sr_key, (uint32_t)pn);
+                a.drho[ctl.base + pn] = s.drho;
                 if (SMODE == 1) {
-                    C* s3 = a.sig3 + 3 * P.base;
+                    C* s3 = a.sig3 + 3 * ctl.base;
                     s3[pn] = s.sxx;
-                    s3[P.P + pn] = s.sxy;
-                    s3[2 * P.P + pn] = s.syy;
+                    s3[ctl.plane + pn] = s.sxy;
+                    s3[2 * ctl.plane + pn] = s.syy;
                 }
                 if (a.flags & F_STORE_SIGMA) {
-                    C* s4 = a.sig4 + 4 * P.base;
+                    C* s4 = a.sig4 + 4 * ctl.base;
                     s4[pn] = s.sxx;
-                    s4[P.P + pn] = s.syy;
-                    s4[2 * P.P + pn] = C(0);
-                    s4[3 * P.P + pn] = s.sxy;
+                    s4[ctl.plane + pn] = s.syy;
+                    s4[2 * ctl.plane + pn] = C(0);
+                    s4[3 * ctl.plane + pn] = s.sxy;
                 }
                 if (a.flags & (F_SAVE_U | F_RESID)) {
                     const C ih = Arith<C>::div(C(1), rho_h);
                     const C urx = jxc * ih, ury = jyc * ih;
-                    C* up_ = a.uprev + 2 * P.base;
+                    C* up_ = a.uprev + 2 * ctl.base;
                     if (a.flags & F_RESID) {
                         const C dx_ = urx - upx_cur, dy_ = ury - upy_cur;
                         const C u2 = urx * urx + ury * ury;
@@ -390,7 +395,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                     }
                     if (a.flags & F_SAVE_U) {
                         up_[pn] = urx;
-                        up_[P.P + pn] = ury;
+                        up_[ctl.plane + pn] = ury;
                     }
                 }
             }
@@ -425,9 +430,10 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         }
     }
 
+    if (vbad) atomicOr(a.status, 1);
     if (bad) {
         // record the timeout and drain this CTA's own copies (bounded) before leaving
-        if (t == 0) {
+        if (t == TI) {
             atomicOr(ctl.timeout_flag, 2);
             for (int k = 0; k < K; ++k)
                 if (last_issued[k] != 0xffffffffu) mbar_wait(&bars[k], (last_issued[k] / K) & 1u, 100000000ull);
