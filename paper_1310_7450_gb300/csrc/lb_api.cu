@@ -300,6 +300,8 @@ struct SweepGroup {
     double tune_ms = 0.0;
 };
 
+constexpr int kDriveRing = 8;  // pinned staging slots of the drive (body force, wall velocity)
+
 struct lb_handle {
     int dev = 0;
     cudaStream_t stream = nullptr;
@@ -334,9 +336,10 @@ struct lb_handle {
     long uprev_state = -10;    // state index whose velocity u_prev holds
     long mon_state = -1;       // state index of the last residual evaluation (-1: none)
     int* status_h = nullptr;   // pinned
-    double* gx_h = nullptr;    // pinned staging of the body forces (h2d each lb_set_body_force)
-    cudaEvent_t gx_ev = nullptr;
-    bool gx_pending = false;
+    double* gx_h = nullptr;              // pinned staging of the drive: kDriveRing slots of 2 n_ch
+    cudaEvent_t gx_ev[kDriveRing] = {};  // values, each reused once its previous copy has run
+    bool gx_pending[kDriveRing] = {};
+    int gx_slot = 0;
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
     bool any_unstable = false;
@@ -601,7 +604,8 @@ void release(lb_handle* h) {
     if (h->status_h) cudaFreeHost(h->status_h);
     if (h->gx_h) cudaFreeHost(h->gx_h);
     if (h->status_ev) cudaEventDestroy(h->status_ev);
-    if (h->gx_ev) cudaEventDestroy(h->gx_ev);
+    for (int k = 0; k < kDriveRing; ++k)
+        if (h->gx_ev[k]) cudaEventDestroy(h->gx_ev[k]);
     for (int k = 0; k < 2; ++k)
         if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -650,16 +654,21 @@ StepArgs<T, C> base_args(lb_handle* h) {
 }
 
 // Body forces and wall velocities: host -> pinned staging -> device -> channel table, all
-// stream-ordered (the staging buffer is reused only after its previous copy ran).
+// stream-ordered.  The staging is a ring of kDriveRing slots, and a slot is reused only after its
+// previous copy ran, so a host that changes the drive every step runs up to kDriveRing steps
+// ahead of the device instead of waiting for the step before.
 lb_status push_drive(lb_handle* h) {
-    if (h->gx_pending) LB_CK(cudaEventSynchronize(h->gx_ev));
+    const int k = h->gx_slot;
+    h->gx_slot = (k + 1) % kDriveRing;
+    if (h->gx_pending[k]) LB_CK(cudaEventSynchronize(h->gx_ev[k]));
+    double* st = h->gx_h + (size_t)k * 2 * h->n_ch;
     for (int c = 0; c < h->n_ch; ++c) {
-        h->gx_h[c] = h->params[c].g_x;
-        h->gx_h[h->n_ch + c] = h->u_wall[c];
+        st[c] = h->params[c].g_x;
+        st[h->n_ch + c] = h->u_wall[c];
     }
-    LB_CK(cudaMemcpyAsync(h->gx_d, h->gx_h, sizeof(double) * 2 * h->n_ch, cudaMemcpyHostToDevice, h->stream));
-    LB_CK(cudaEventRecord(h->gx_ev, h->stream));
-    h->gx_pending = true;
+    LB_CK(cudaMemcpyAsync(h->gx_d, st, sizeof(double) * 2 * h->n_ch, cudaMemcpyHostToDevice, h->stream));
+    LB_CK(cudaEventRecord(h->gx_ev[k], h->stream));
+    h->gx_pending[k] = true;
     if (h->csize == 8) k_apply_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->gx_d, h->n_ch, h->nx);
     else k_apply_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->gx_d, h->n_ch, h->nx);
     LB_CK(cudaGetLastError());
@@ -1317,10 +1326,10 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
 #undef LB_ALLOC
     e = cudaMallocHost((void**)&h->status_h, h->n_ch * sizeof(int));
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
-    e = cudaMallocHost((void**)&h->gx_h, 2 * h->n_ch * sizeof(double));
+    e = cudaMallocHost((void**)&h->gx_h, (size_t)kDriveRing * 2 * h->n_ch * sizeof(double));
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
     e = cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gx_ev, cudaEventDisableTiming);
+    for (int k = 0; k < kDriveRing && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&h->gx_ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaEventCreate"));
 
     // tables (synchronous copies: creation is not on the hot path)
