@@ -69,6 +69,14 @@ extern template cudaError_t march_occupancy<float, float, 0, 1>(int*);
 extern template cudaError_t march_occupancy<float, float, 1, 1>(int*);
 extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0, 1>(int*);
 extern template cudaError_t march_occupancy<__nv_bfloat16, float, 1, 1>(int*);
+extern template cudaError_t launch_step_march<float, float, 0, 2>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<float, float, 1, 2>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0, 2>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<__nv_bfloat16, float, 1, 2>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t march_occupancy<float, float, 0, 2>(int*);
+extern template cudaError_t march_occupancy<float, float, 1, 2>(int*);
+extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0, 2>(int*);
+extern template cudaError_t march_occupancy<__nv_bfloat16, float, 1, 2>(int*);
 }  // namespace lbk
 
 using namespace lbk;
@@ -509,10 +517,12 @@ lb_status plan_march(lb_handle* h) {
     if (e == cudaSuccess) {
         const bool bnd = h->gpbc || h->moving;
         if (h->prec == LB_PREC_F32) {
-            if (bnd) e = h->smode ? march_occupancy<float, float, 1, 1>(&bps) : march_occupancy<float, float, 0, 1>(&bps);
+            if (h->gpbc) e = h->smode ? march_occupancy<float, float, 1, 1>(&bps) : march_occupancy<float, float, 0, 1>(&bps);
+            else if (bnd) e = h->smode ? march_occupancy<float, float, 1, 2>(&bps) : march_occupancy<float, float, 0, 2>(&bps);
             else e = h->smode ? march_occupancy<float, float, 1>(&bps) : march_occupancy<float, float, 0>(&bps);
         } else {
-            if (bnd) e = h->smode ? march_occupancy<__nv_bfloat16, float, 1, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0, 1>(&bps);
+            if (h->gpbc) e = h->smode ? march_occupancy<__nv_bfloat16, float, 1, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0, 1>(&bps);
+            else if (bnd) e = h->smode ? march_occupancy<__nv_bfloat16, float, 1, 2>(&bps) : march_occupancy<__nv_bfloat16, float, 0, 2>(&bps);
             else e = h->smode ? march_occupancy<__nv_bfloat16, float, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0>(&bps);
         }
     }
@@ -697,9 +707,12 @@ template <>
 cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float>& a) {
     MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0]};
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
-    if (h->gpbc || h->moving)
+    if (h->gpbc)
         return h->smode ? launch_step_march<float, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
                         : launch_step_march<float, float, 0, 1>(m, a, ctl, h->march_grid, h->stream);
+    if (h->moving)
+        return h->smode ? launch_step_march<float, float, 1, 2>(m, a, ctl, h->march_grid, h->stream)
+                        : launch_step_march<float, float, 0, 2>(m, a, ctl, h->march_grid, h->stream);
     return h->smode ? launch_step_march<float, float, 1>(m, a, ctl, h->march_grid, h->stream)
                     : launch_step_march<float, float, 0>(m, a, ctl, h->march_grid, h->stream);
 }
@@ -707,9 +720,12 @@ template <>
 cudaError_t launch_march<__nv_bfloat16, float>(lb_handle* h, const StepArgs<__nv_bfloat16, float>& a) {
     MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0]};
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
-    if (h->gpbc || h->moving)
+    if (h->gpbc)
         return h->smode ? launch_step_march<__nv_bfloat16, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
                         : launch_step_march<__nv_bfloat16, float, 0, 1>(m, a, ctl, h->march_grid, h->stream);
+    if (h->moving)
+        return h->smode ? launch_step_march<__nv_bfloat16, float, 1, 2>(m, a, ctl, h->march_grid, h->stream)
+                        : launch_step_march<__nv_bfloat16, float, 0, 2>(m, a, ctl, h->march_grid, h->stream);
     return h->smode ? launch_step_march<__nv_bfloat16, float, 1>(m, a, ctl, h->march_grid, h->stream)
                     : launch_step_march<__nv_bfloat16, float, 0>(m, a, ctl, h->march_grid, h->stream);
 }

@@ -99,9 +99,10 @@ constexpr size_t march_smem_bytes() {
     return 128 /*barriers*/ + K * slot + (size_t)4 * (W + 2) * 2 * sizeof(C);
 }
 
-// BND = 1: channel ends joined by the generalized periodic boundaries of Sec. II B and / or a
-// moving Couette wall on the last row (Sec. IV C), both applied where the populations are pulled
-// (the same rules as the tile kernel's pull9); BND = 0: periodic x and bounce-back walls only.
+// BND = 1: channel ends joined by the generalized periodic boundaries of Sec. II B, and a moving
+// Couette wall on the last row (Sec. IV C) if the channel has one; BND = 2: the moving wall only;
+// both applied where the populations are pulled (the same rules as the tile kernel's pull9).
+// BND = 0: periodic x and bounce-back walls only.
 template <typename T, typename C, int SMODE, int W, int K, int BND = 0>
 __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUtensorMap tmap, const StepArgs<T, C> a,
                                                   const MarchCtl ctl) {
@@ -123,10 +124,16 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
     if (a.status[0] != 0) return;
 
     __shared__ int s_bad;  // set by any thread whose bounded wait gave up; read after a barrier
+    __shared__ C s_delta[2];  // BND == 1 with GPBC: rho_out - mean(x = 0), rho_in - mean(x = nx-1)
     constexpr int TI = W - 32;  // the thread that issues the copies (lane 0 of the last warp;
                                 // warp 0 computes the halo columns)
     if (t == 0) {
         s_bad = 0;
+        if (BND == 1 && a.gcol != nullptr) {
+            const C* means = a.gcol + 6LL * a.gny;  // [channel][column] means of rho - 1
+            s_delta[0] = P.rho_out - means[0];
+            s_delta[1] = P.rho_in - means[1];
+        }
         prefetch_tmap(&tmap);
         for (int k = 0; k < K; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
@@ -201,30 +208,39 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                 }
             }
             if constexpr (BND == 1) {
-                // (channel data are re-read here rather than kept live: only edge nodes and the
-                // wall row need them)
                 if ((left_edge || right_edge) && a.gcol != nullptr) {
                     // the node's true column; the slots hold the raw periodic images, so every
                     // population that crosses an end gets its shift here (Sec. II B)
                     const int xg = x0 + col;
                     const int X = xg < 0 ? xg + nx : (xg >= nx ? xg - nx : xg);
                     if (X == 0 || X == nx - 1) {
-                        const ChanParams<C>& Q = a.chan[0];
-                        const C* gc = a.gcol + Q.row_off;
-                        const C* means = a.gcol + 6LL * a.gny;
-                        const C dplus = Q.rho_in - means[1], dminus = Q.rho_out - means[0];
+                        // populations entering at x = 0 move with c_x = +1 and leave the column
+                        // x = nx-1 (boundary column c = 1); those entering at x = nx-1 move with
+                        // c_x = -1 and leave x = 0 (c = 0).  The column data of the three source
+                        // rows are loaded together, before any shift is formed.
+                        const int c = X == 0 ? 1 : 0;
+                        const int sx = X == 0 ? 1 : -1;
+                        const C delta = s_delta[c];
+                        const C* gc = a.gcol + P.row_off + c * a.gny;
+                        C gr[3], gjx[3], gjy[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {  // source row r - 1 + k, k = 1 - c_y
+                            const int ys = r - 1 + k;
+                            const bool in = ys >= 0 && ys < ny;
+                            gr[k] = in ? gc[ys] : C(0);
+                            gjx[k] = in ? gc[2 * a.gny + ys] : C(0);
+                            gjy[k] = in ? gc[4 * a.gny + ys] : C(0);
+                        }
 #pragma unroll
                         for (int i = 1; i < 9; ++i) {
-                            if (cx(i) == 0) continue;
                             const int ys = r - cy(i);
-                            const int xr = X - cx(i);
-                            if (ys < 0 || ys >= ny || (xr >= 0 && xr < nx)) continue;
-                            const int c = xr < 0 ? 1 : 0;
-                            d[i] += gpbc_shift<C>(i, gc[c * a.gny + ys], gc[(2 + c) * a.gny + ys],
-                                                  gc[(4 + c) * a.gny + ys], xr < 0 ? dplus : dminus);
+                            if (cx(i) != sx || ys < 0 || ys >= ny) continue;
+                            d[i] += gpbc_shift<C>(i, gr[1 - cy(i)], gjx[1 - cy(i)], gjy[1 - cy(i)], delta);
                         }
                     }
                 }
+            }
+            if constexpr (BND >= 1) {
                 if (r == ny - 1 && a.chan[0].moving) zou_he_top<C>(d, a.chan[0].u_wall);
             }
         };
