@@ -190,15 +190,12 @@ template <> struct Arith<float> {
     }
 };
 
-// Moments of Eq. (rhoj) from the post-streaming deviations: dR = sum_i n_i - 1, J0 = sum c_i n_i,
-// from the partial sums over the directions with c_x = +1, -1 and c_y = +1, -1 (14 additions).
+// Moments of Eq. (rhoj) from the post-streaming deviations: dR = sum_i n_i - 1, J0 = sum c_i n_i.
 template <typename C>
 __device__ __forceinline__ void moments(const C (&d)[9], C& dR, C& jx, C& jy) {
-    const C xp = d[1] + (d[5] + d[8]), xm = d[3] + (d[6] + d[7]);
-    const C yp = d[2] + (d[5] + d[6]), ym = d[4] + (d[7] + d[8]);
-    jx = xp - xm;
-    jy = yp - ym;
-    dR = (d[0] + (d[2] + d[4])) + (xp + xm);
+    dR = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
 }
 
 // Velocity used for the gradients (reading: j / R0 with R0 = sum_i n_i after streaming, because
