@@ -182,3 +182,42 @@ def test_equilibrium_offset_form(oracle_mod):
         full = oracle_mod.equilibrium(rho, u[0], u[1]) - oracle_mod.WEIGHTS
         off = oracle_mod.equilibrium_offset(rho - 1.0, u[0], u[1])
         np.testing.assert_allclose(off, full, rtol=0, atol=2e-16)
+
+
+def test_time_stepped_stress_transient_simple_shear(oracle_mod):
+    """Stress mode 1 from rest under steady simple shear (kappa_xy = gdot): the backward-Euler
+    recursion of Eq. (gkder), (1 + 1/tau_M) s' - (kappa s' + s' kappa^T) = s + G D, decouples into
+    s_yy = 0, s_xy(n) = a (s_xy(n-1) + G gdot) and s_xx(n) = a (s_xx(n-1) + 2 gdot s_xy(n)),
+    a = tau_M/(tau_M + 1), solved by hand:
+      s_xy(n) = Y (1 - a^n),  s_xx(n) = 2 a gdot Y [(1 - a^n)/(1 - a) - n a^n],  Y = G gdot tau_M,
+    whose limits are the simple-shear sigma_xy and N1 = 2 G gdot^2 tau_M^2."""
+    G = 1e-3
+    for gdot, tau_M in [(1e-3, 7.0), (4e-3, 40.0), (-2e-3, 1.5)]:
+        a = tau_M / (tau_M + 1.0)
+        Y = G * gdot * tau_M
+        s = np.zeros(3)
+        for n in range(1, 400):
+            s = oracle_mod.stress_step([0.0, gdot, 0.0, 0.0], tau_M, G, s)
+            want_xy = Y * (1.0 - a ** n)
+            want_xx = 2.0 * a * gdot * Y * ((1.0 - a ** n) / (1.0 - a) - n * a ** n)
+            assert s[2] == 0.0
+            assert s[1] == pytest.approx(want_xy, rel=1e-12, abs=1e-22)
+            assert s[0] == pytest.approx(want_xx, rel=1e-11, abs=1e-22)
+
+
+def test_time_stepped_stress_transient_planar_extension(oracle_mod):
+    """Stress mode 1 from rest under planar extension (kappa = diag(e, -e)): the normal components
+    relax geometrically, s_xx(n) = X (1 - bx^n) with bx = 1/(1 + 1/tau_M - 2e) and X = 2 G e tau_M /
+    (1 - 2 e tau_M) (the steady planar-extension stress), s_yy likewise with -e, s_xy = 0."""
+    G = 1e-3
+    for e, tau_M in [(1e-3, 20.0), (-3e-3, 9.0)]:
+        bx = 1.0 / (1.0 + 1.0 / tau_M - 2.0 * e)
+        by = 1.0 / (1.0 + 1.0 / tau_M + 2.0 * e)
+        X = 2.0 * G * e * tau_M / (1.0 - 2.0 * e * tau_M)
+        Yy = -2.0 * G * e * tau_M / (1.0 + 2.0 * e * tau_M)
+        s = np.zeros(3)
+        for n in range(1, 300):
+            s = oracle_mod.stress_step([e, 0.0, 0.0, -e], tau_M, G, s)
+            assert s[0] == pytest.approx(X * (1.0 - bx ** n), rel=1e-12)
+            assert s[2] == pytest.approx(Yy * (1.0 - by ** n), rel=1e-12)
+            assert s[1] == 0.0
