@@ -40,6 +40,9 @@ def kernel_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
+PREC_NAME = {"f32": "FP32", "bf16": "BF16", "f64": "FP64"}
+
+
 def bytes_per_node(precision: str, store_sigma: bool, stress_mode: int) -> int:
     """Algorithmic HBM bytes per node and step: 9 population loads + 9 stores in the storage type,
     delta rho read + write, (+ stress write), (+ carried stress read + write in stress mode 1)."""
@@ -311,7 +314,8 @@ def run_gpu(args):
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision, "data": "synthetic",
             "config": {"workload": f"single large channel {nx}x{ny} start-up, nlM theta=100, gamma_c=0.1, "
-                                   f"tau_LB=0.9, g=1e-6, G_inf=1e-3; FP32 SoA deviations + 4-component stress"
+                                   f"tau_LB=0.9, g=1e-6, G_inf=1e-3; {PREC_NAME[args.precision]} SoA deviations"
+                                   + (" + 4-component stress" if args.store_sigma else "")
                                    + ("" if args.x_mode == "periodic" else "; pressure-driven ends (GPBC)")
                                    + ("" if args.walls == "bounce_back" else f"; Couette wall u={args.u_wall:g}"),
                        "x_mode": args.x_mode, "walls": args.walls, "kernel": kernel,
