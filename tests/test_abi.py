@@ -64,3 +64,43 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lb_step_count(None) == -1
     assert lib.lb_num_nodes(None) == 0
     lib.lb_destroy(None)
+
+
+@pytest.mark.parametrize("bnd", [dict(x_mode=0), dict(x_mode=3), dict(walls=0), dict(walls=5)])
+def test_invalid_boundary_rejected_before_any_device_work(lib, bnd):
+    from paper_1310_7450_gb300 import lbnlm
+    p = dict(tau_lb=0.9, g_x=1e-6, G_inf=1e-3, tau0=1.0, theta=10.0, gamma_c=0.1, rho0=1.0)
+    with pytest.raises(lbnlm.LBError) as e:
+        lbnlm.lb_create(4, 16, p, 0, 0, **bnd)
+    assert e.value.status == lbnlm.LB_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the built library every call raises."""
+    from paper_1310_7450_gb300 import lbnlm
+    monkeypatch.setattr(lbnlm, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "liblbnlm.so"))
+    monkeypatch.setattr(lbnlm, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        lbnlm.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        lbnlm.lb_strerror(0)
+
+
+def _gpu_present():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(_gpu_present(), reason="checks the behaviour on a machine without a GPU")
+def test_no_cpu_fallback_without_a_gpu(lib):
+    """A valid configuration on a machine without a usable GPU fails with LB_ECUDA and a message;
+    nothing is computed on the host."""
+    from paper_1310_7450_gb300 import lbnlm
+    p = dict(tau_lb=0.9, g_x=1e-6, G_inf=1e-3, tau0=1.0, theta=10.0, gamma_c=0.1, rho0=1.0)
+    with pytest.raises(lbnlm.LBError) as e:
+        lbnlm.lb_create(4, 16, p, 0, 0)
+    assert e.value.status == lbnlm.LB_ECUDA
+    assert "lb_create" in lbnlm.lb_last_error()
