@@ -145,10 +145,10 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
     bool bad = false;
 
     auto slot_ptr = [&](uint32_t idx) -> const T* { return reinterpret_cast<const T*>(slots + (idx % K) * SLOT); };
-    uint32_t last_issued[K];  // thread 0: index of the last copy issued into each slot
+    uint32_t last_issued[K];  // issuing thread: index of the last copy issued into each slot
 #pragma unroll
     for (int k = 0; k < K; ++k) last_issued[k] = 0xffffffffu;
-    auto issue = [&](uint32_t idx, int x0, int row) {  // thread 0 only
+    auto issue = [&](uint32_t idx, int x0, int row) {  // issuing thread (TI) only
         uint64_t* b = &bars[idx % K];
         mbar_expect_tx(b, TX);
         tma_load_3d(slots + (idx % K) * SLOT, &tmap, b, x0 - HP, row, 0);

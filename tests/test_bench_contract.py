@@ -57,3 +57,10 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["config"]["nx"] == 32 and line["config"]["ny"] == 32
+
+
+def test_kernel_hash_covers_code_not_comments():
+    b = load_bench()
+    src = "int f(int a) {  // one\n    /* two\n       lines */\n    return a + 1;\n}\n"
+    assert b.code_only(src) == b.code_only(src.replace("one", "uno").replace("two", "dos") + "\n// more\n")
+    assert b.code_only(src) != b.code_only(src.replace("a + 1", "a + 2"))
