@@ -225,8 +225,8 @@ def run_gpu(args):
         lbnlm.lb_set_wall_velocity(sim.h, -1, args.u_wall)
     nodes = nx * ny
     kernel = "k_step_march" if lbnlm.lb_uses_row_march(sim.h) else "k_step_tile"
-    # the tile kernel also launches one boundary-column kernel per step for pressure-driven ends
-    launches_per_step = 2 if (args.x_mode == "gpbc" and kernel == "k_step_tile") else 1
+    # pressure-driven ends add one boundary-column kernel before every step (either step kernel)
+    launches_per_step = 2 if args.x_mode == "gpbc" else 1
 
     def barrier():
         if ws > 1:
