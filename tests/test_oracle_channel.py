@@ -165,6 +165,20 @@ def test_mirror_symmetry_and_x_invariance(oracle_mod):
     assert np.abs(u[:, :, 1]).max() <= 1e-10 * np.abs(ux).max()
 
 
+def test_threads_do_not_change_the_result(oracle_mod):
+    """The oracle's OpenMP split over rows (used for the timed CPU baseline) updates every node from
+    the same inputs in the same order of operations: 1, 3 and 8 threads give bitwise equal states."""
+    nx, ny = 9, 23
+    p = inputs.matched_params(0.9, 10.0, 0.1, 1e-3, 1e-5)
+    out = []
+    for nt in (1, 3, 8):
+        st = random_state(oracle_mod, nx, ny, 33)
+        oracle_mod.run(p, st, 40, nthreads=nt)
+        out.append((st.dev.copy(), st.drho.copy()))
+    for dev, drho in out[1:]:
+        assert np.array_equal(dev, out[0][0]) and np.array_equal(drho, out[0][1])
+
+
 @pytest.mark.parametrize("ny", [3, 4, 5, 8])
 def test_bruteforce_twin_tiny_grids(oracle_mod, ny):
     """The independently written NumPy twin (push streaming, 4x4 Kronecker stress solve) agrees
