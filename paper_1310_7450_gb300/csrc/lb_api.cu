@@ -9,6 +9,7 @@
 //   velocity: 2 planes.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -309,6 +310,15 @@ struct SweepGroup {
 };
 
 constexpr int kDriveRing = 8;  // pinned staging slots of the drive (body force, wall velocity)
+
+// NVTX range over a public call, so that profiler timelines (Nsight Systems / Compute) group the
+// launches of one lb_step or sweep; a no-op unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct lb_handle {
     int dev = 0;
@@ -1122,6 +1132,7 @@ const char* lb_last_error(void) { return g_err; }
 
 lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long max_steps, long long* steps_out,
                               double* residual_out) {
+    NvtxRange range("lb_run_until_steady");
     if (!h || check_every < 2 || (check_every & 1) || max_steps < check_every || std::isnan(tol))
         return fail(LB_EINVAL, "lb_run_until_steady: need an even check_every >= 2 and max_steps >= check_every%s");
     if (h->smode != 0) return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements stress mode 0%s");
@@ -1191,6 +1202,7 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
 }
 
 lb_status lb_sweep_tune(lb_handle* h) {
+    NvtxRange range("lb_sweep_tune");
     if (!h) return fail(LB_EINVAL, "lb_sweep_tune: null handle%s");
     if (h->smode != 0) return fail(LB_EINVAL, "lb_sweep_tune: the sweep kernel implements stress mode 0%s");
     if (h->gpbc || h->moving)
@@ -1408,6 +1420,7 @@ long lb_graph_replays(const lb_handle* h) { return h ? h->graph_replays : -1; }
 size_t lb_num_nodes(const lb_handle* h) { return h ? (size_t)h->nodes : 0; }
 
 lb_status lb_step(lb_handle* h, long n) {
+    NvtxRange range("lb_step");
     if (!h || n < 0) return fail(LB_EINVAL, "lb_step: bad handle or n%s");
     lb_status st = poll_status(h, false);
     if (st != LB_OK) return st;
