@@ -18,6 +18,10 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
     stress_series    pinned: simple-shear / extension / yield-stress closed forms of Sec. III A,
                      and against the separately written elimination
     stress_step      pinned: its fixed point is the steady solution of Eq. (sigtsum)
+    intermediates    pinned directly: the three-point gradients (Sec. II C) are exact on a planted
+                     quadratic velocity, wall rows included; the delta rho of Eq. (rhoplus) makes
+                     the hydrodynamic density uniform in a steady channel while rho_eq + 3/2 N1 is
+                     constant (tests/test_oracle_gradients_density.py)
     run / fields     pinned: Newtonian parabola and start-up series, analytic nlM channel profile
                      (Eq. maxwellpoiseuille), mass conservation, mirror symmetry, Newtonian
                      equivalence of the forcing (below Eq. bodyforce), brute-force twin
