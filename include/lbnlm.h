@@ -143,12 +143,25 @@ lb_status lb_get_fields(lb_handle *h, void *u, void *sigma, void *rho, int out_d
 
 /* Per-channel one-step residual ||u(t) - u(t-1)||_2 / ||u(t)||_2 of the state before the last
  * step of the most recent lb_step call (warp/block reductions fused into that step).
- * r: host [n_channels].  LB_ESTATE if no residual has been evaluated yet. */
+ * r: host [n_channels].  LB_ESTATE if no residual has been evaluated yet, or if the last
+ * evaluation was taken in LB_MONITOR_FLUX_MAX mode. */
 lb_status lb_residual(lb_handle *h, double *r);
 
 /* Per-channel diagnostics of the same evaluation, host [n_channels][4]:
- * (residual, flux = sum over nodes of u_x / nx, max |u|, step index of the evaluated state). */
+ * (residual, flux = sum over nodes of u_x / nx, max |u|, step index of the evaluated state).
+ * The residual slot holds -1 when the evaluation was taken in LB_MONITOR_FLUX_MAX mode, NaN for
+ * a channel whose status word is set. */
 lb_status lb_monitor(lb_handle *h, double *out);
+
+/* What the last step of each lb_step call evaluates (not in the paper: run control).
+ * LB_MONITOR_RESIDUAL (default): the last two steps save the velocity and the last one forms the
+ * residual, flux and max |u| (16 B per node more HBM traffic on the saving steps, 16 B more
+ * again on the residual step).  LB_MONITOR_FLUX_MAX: the last step forms flux and max |u| only,
+ * from its own state, at the traffic of a plain step -- what a cessation run needs every step
+ * (its stop is max |u| < 1e-10); lb_monitor then reports -1 as the residual and lb_residual
+ * returns LB_ESTATE.  LB_EINVAL for another mode. */
+enum { LB_MONITOR_RESIDUAL = 0, LB_MONITOR_FLUX_MAX = 1 };
+lb_status lb_set_monitor_mode(lb_handle *h, int mode);
 
 /* The same diagnostics without waiting: enqueues their copy into out ([n_channels][4], pinned
  * host memory or device memory) on the handle's stream and returns at once.  The values are
@@ -182,7 +195,11 @@ lb_status lb_get_populations(lb_handle *h, double *n, double *drho, double *sig3
 
 /* Checkpoint: the raw device state (populations in storage precision, delta rho, carried
  * stress, step counter) as an opaque byte image of lb_state_bytes() bytes.  Restoring it into a
- * handle created with the same grid continues bit-for-bit. */
+ * handle created with the same grid continues bit-for-bit.  lb_set_state rejects (LB_EINVAL) an
+ * image of another library version, grid, precision, stress mode or per-channel ny list (the
+ * header carries a hash of the list, so channels [24, 40] never load an image of [40, 24]), and
+ * clears the per-channel status word and the sticky LB_EUNSTABLE / LB_ETIMEOUT state: rolling
+ * back to an image taken before an instability steps every channel again. */
 size_t lb_state_bytes(const lb_handle *h);
 lb_status lb_get_state(lb_handle *h, void *buf, size_t bytes);
 lb_status lb_set_state(lb_handle *h, const void *buf, size_t bytes);
@@ -239,10 +256,14 @@ lb_status lb_sweep_set_config(lb_handle *h, int variant, int threads, int cluste
  * (residual ||u_now - u_prev||_2/||u_now||_2, flux = sum of u_x / nx, max |u|) to out (device,
  * [n_channels][3], double), on cuda_stream.  It calls no allocating routine: its scratch is a fixed
  * 2 MiB array inside the library (65536 records; at most 1024 channels per call, larger requests
- * fail with LB_EINVAL) that every GPU using the library keeps until the process exits.  The first
- * call on a device looks the array up (cudaGetSymbolAddress); make that call before any stream
- * capture.  Calls share the array, so calls that overlap on the GPU (e.g. on two streams) race;
- * each call writes every scratch record it reads, so nothing needs clearing between calls. */
+ * fail with LB_EINVAL) that every GPU using the library keeps until the process exits.  Each call
+ * on a stream that is not capturing looks the array's address up (cudaGetSymbolAddress, with the
+ * current device); the first call on a device must come before any stream capture (LB_ESTATE
+ * otherwise).  cuda_stream (NULL = legacy default stream) must belong to the current device
+ * (LB_EINVAL otherwise).  Calls share the array, so calls that overlap on the GPU (e.g. on two
+ * streams) race; each call writes every scratch record it reads, so nothing needs clearing
+ * between calls.  A NaN or Inf anywhere in a channel's u_now or u_prev makes all three of that
+ * channel's outputs NaN; a channel at rest (u_now = 0) reports residual 0. */
 lb_status lb_field_monitor_static(const void *u_now, const void *u_prev, int dtype, int n_channels,
                                   const long long *node_offsets, int nx, double *out, void *cuda_stream);
 
@@ -262,6 +283,13 @@ lb_status lb_mlp_gradients(lb_mlp *m, const float *x, const float *target, int b
 lb_status lb_mlp_train_step(lb_mlp *m, const float *x, const float *target, int batch, float lr, double *loss);
 lb_status lb_mlp_get_params(lb_mlp *m, float *host);        /* FP32 masters -> host [n_params]     */
 lb_status lb_mlp_set_params(lb_mlp *m, const float *host);  /* host [n_params] -> masters and BF16 */
+
+/* Limit of every bounded device-side wait of the row-march step kernel (the mbarrier waits for its
+ * row copies), in seconds: 0 <= seconds <= 60, default 2.  0 makes each wait a single non-blocking
+ * probe.  A wait that gives up sets bit 2 of the channel's status word; the kernel then waits (at
+ * most 1 s, independent of this limit) for its own copies in flight and returns, and the next
+ * lb_step reports LB_ETIMEOUT.  Not in the paper: failure detection of this library's kernels. */
+lb_status lb_set_wait_limit(lb_handle *h, double seconds);
 
 long lb_step_count(const lb_handle *h);     /* steps taken since creation (or restored)      */
 int lb_uses_row_march(const lb_handle *h);  /* 1 if plain steps run on the row-march kernel   */

@@ -239,8 +239,9 @@ __global__ void k_apply_gx(ChanParams<C>* chan, const double* gx, int n_ch, int 
 }
 
 // Per-channel reduction of the step's block partials, in a fixed order (deterministic).
+// with_residual = 0: the partials hold flux and max |u| only (F_MON); the residual slot reads -1
 __global__ void k_reduce_residual(const double* partials, const int* item_begin, const int* status, double* mon,
-                                  int nx, long long state_index) {
+                                  int nx, long long state_index, int with_residual) {
     const int c = blockIdx.x;
     const int b = item_begin[c], e = item_begin[c + 1];
     __shared__ double red[kThreads][4];
@@ -264,7 +265,7 @@ __global__ void k_reduce_residual(const double* partials, const int* item_begin,
     }
     if (threadIdx.x == 0) {
         const bool ok = status[c] == 0;
-        mon[4 * c + 0] = ok ? (red[0][1] > 0 ? sqrt(red[0][0] / red[0][1]) : 0.0) : NAN;
+        mon[4 * c + 0] = !ok ? NAN : (!with_residual ? -1.0 : (red[0][1] > 0 ? sqrt(red[0][0] / red[0][1]) : 0.0));
         mon[4 * c + 1] = ok ? red[0][2] / nx : NAN;
         mon[4 * c + 2] = ok ? red[0][3] : NAN;
         mon[4 * c + 3] = (double)state_index;
@@ -352,7 +353,9 @@ struct lb_handle {
     // bookkeeping
     long step = 0;
     long uprev_state = -10;    // state index whose velocity u_prev holds
-    long mon_state = -1;       // state index of the last residual evaluation (-1: none)
+    long mon_state = -1;       // state index of the last monitor evaluation (-1: none)
+    bool mon_resid = false;    // the last monitor evaluation includes the residual
+    int monitor_mode = 0;      // LB_MONITOR_RESIDUAL or LB_MONITOR_FLUX_MAX
     int* status_h = nullptr;   // pinned
     double* gx_h = nullptr;              // pinned staging of the drive: kDriveRing slots of 2 n_ch
     cudaEvent_t gx_ev[kDriveRing] = {};  // values, each reused once its previous copy has run
@@ -362,6 +365,7 @@ struct lb_handle {
     bool status_pending = false;
     bool any_unstable = false;
     bool any_timeout = false;
+    unsigned long long wait_ns = 2000000000ull;  // limit of the row-march kernel's mbarrier waits
     // row-march kernel (wide single channels, FP32 / BF16 storage)
     bool march = false;
     CUtensorMap mapA, mapB;    // tensor maps of the two population buffers ...
@@ -715,7 +719,7 @@ template <typename T, typename C>
 cudaError_t launch_march(lb_handle*, const StepArgs<T, C>&) { return cudaErrorNotSupported; }
 template <>
 cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float>& a) {
-    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0]};
+    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0], h->wait_ns};
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
     if (h->gpbc)
         return h->smode ? launch_step_march<float, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
@@ -728,7 +732,7 @@ cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float
 }
 template <>
 cudaError_t launch_march<__nv_bfloat16, float>(lb_handle* h, const StepArgs<__nv_bfloat16, float>& a) {
-    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0]};
+    MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0], h->wait_ns};
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
     if (h->gpbc)
         return h->smode ? launch_step_march<__nv_bfloat16, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
@@ -807,18 +811,25 @@ lb_status run_steps(lb_handle* h, long n) {
         if (h->flags & LB_GRID_STORE_SIGMA) f |= F_STORE_SIGMA;
         if (sr) f |= F_SR;
         a.sr_key = step_key(h, h->step);
-        const bool resid = (s == n) && (h->uprev_state == h->step - 1);
-        if (s >= n - 1) f |= F_SAVE_U;
-        if (resid) f |= F_RESID;
+        bool resid = false, mon = false;
+        if (h->monitor_mode == LB_MONITOR_FLUX_MAX) {
+            mon = (s == n);  // flux and max |u| of the last step's state: no saved velocity
+            if (mon) f |= F_MON;
+        } else {
+            resid = mon = (s == n) && (h->uprev_state == h->step - 1);
+            if (s >= n - 1) f |= F_SAVE_U;
+            if (resid) f |= F_RESID;
+        }
         a.flags = f;
         LB_CK((gpbc_columns<T, C>(h)));
         if (h->march) LB_CK((launch_march<T, C>(h, a)));
         else LB_CK((launch<T, C>(h, a)));
-        if (resid) {
+        if (mon) {
             k_reduce_residual<<<h->n_ch, kThreads, 0, h->stream>>>(h->partials, h->march ? h->march_item_begin_d : h->item_begin_d,
-                                                                    h->status_d, h->mon_d, h->nx, h->step);
+                                                                    h->status_d, h->mon_d, h->nx, h->step, resid ? 1 : 0);
             LB_CK(cudaGetLastError());
             h->mon_state = h->step;
+            h->mon_resid = resid;
         }
         if (f & F_SAVE_U) h->uprev_state = h->step;
         std::swap(h->popA, h->popB);
@@ -1414,6 +1425,12 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
 
 void lb_destroy(lb_handle* h) { release(h); }
 
+lb_status lb_set_wait_limit(lb_handle* h, double seconds) {
+    if (!h || !(seconds >= 0.0) || seconds > 60.0) return fail(LB_EINVAL, "lb_set_wait_limit: need 0 <= seconds <= 60%s");
+    h->wait_ns = (unsigned long long)(seconds * 1e9);
+    return LB_OK;
+}
+
 long lb_step_count(const lb_handle* h) { return h ? h->step : -1; }
 int lb_uses_row_march(const lb_handle* h) { return (h && h->march) ? 1 : 0; }
 long lb_graph_replays(const lb_handle* h) { return h ? h->graph_replays : -1; }
@@ -1467,7 +1484,7 @@ lb_status lb_get_fields(lb_handle* h, void* u, void* sigma, void* rho, int out_d
 
 lb_status lb_monitor(lb_handle* h, double* out) {
     if (!h || !out) return fail(LB_EINVAL, "lb_monitor: null argument%s");
-    if (h->mon_state < 0) return fail(LB_ESTATE, "lb_monitor: no residual evaluated yet (run lb_step with n >= 2)%s");
+    if (h->mon_state < 0) return fail(LB_ESTATE, "lb_monitor: no monitor evaluated yet (run lb_step with n >= 2)%s");
     LB_CK(cudaMemcpyAsync(out, h->mon_d, 4 * h->n_ch * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     return LB_OK;
@@ -1475,13 +1492,22 @@ lb_status lb_monitor(lb_handle* h, double* out) {
 
 lb_status lb_monitor_async(lb_handle* h, double* out) {
     if (!h || !out) return fail(LB_EINVAL, "lb_monitor_async: null argument%s");
-    if (h->mon_state < 0) return fail(LB_ESTATE, "lb_monitor_async: no residual evaluated yet (run lb_step with n >= 2)%s");
+    if (h->mon_state < 0) return fail(LB_ESTATE, "lb_monitor_async: no monitor evaluated yet (run lb_step with n >= 2)%s");
     LB_CK(cudaMemcpyAsync(out, h->mon_d, 4 * h->n_ch * sizeof(double), cudaMemcpyDefault, h->stream));
+    return LB_OK;
+}
+
+lb_status lb_set_monitor_mode(lb_handle* h, int mode) {
+    if (!h || (mode != LB_MONITOR_RESIDUAL && mode != LB_MONITOR_FLUX_MAX))
+        return fail(LB_EINVAL, "lb_set_monitor_mode: bad handle or mode%s");
+    h->monitor_mode = mode;
     return LB_OK;
 }
 
 lb_status lb_residual(lb_handle* h, double* r) {
     if (!h || !r) return fail(LB_EINVAL, "lb_residual: null argument%s");
+    if (h->mon_state >= 0 && !h->mon_resid)
+        return fail(LB_ESTATE, "lb_residual: the last monitor evaluation had no residual (LB_MONITOR_FLUX_MAX)%s");
     std::vector<double> m(4 * (size_t)h->n_ch);
     lb_status st = lb_monitor(h, m.data());
     if (st != LB_OK) return st;
@@ -1606,8 +1632,20 @@ struct StateHeader {
     uint64_t magic, version;
     int64_t step, planes;
     int32_t n_ch, nx, prec, smode;
+    uint64_t ny_hash;  // FNV-1a of the per-channel ny list: the image's channel split
 };
 constexpr uint64_t kMagic = 0x4d4c4e2d424c6772ull;
+constexpr uint64_t kStateVersion = 2;
+
+uint64_t ny_list_hash(const std::vector<int>& ny) {
+    uint64_t x = 0xcbf29ce484222325ull;  // FNV-1a, 64-bit offset basis and prime
+    for (int v : ny)
+        for (int b = 0; b < 4; ++b) {
+            x ^= (uint64_t)(((uint32_t)v >> (8 * b)) & 0xffu);
+            x *= 0x100000001b3ull;
+        }
+    return x;
+}
 }  // namespace
 
 size_t lb_state_bytes(const lb_handle* h) {
@@ -1619,7 +1657,7 @@ size_t lb_state_bytes(const lb_handle* h) {
 
 lb_status lb_get_state(lb_handle* h, void* buf, size_t bytes) {
     if (!h || !buf || bytes < lb_state_bytes(h)) return fail(LB_EINVAL, "lb_get_state: bad buffer%s");
-    StateHeader hd{kMagic, 1, h->step, h->planes, h->n_ch, h->nx, h->prec, h->smode};
+    StateHeader hd{kMagic, kStateVersion, h->step, h->planes, h->n_ch, h->nx, h->prec, h->smode, ny_list_hash(h->ny)};
     char* p = (char*)buf;
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -1636,16 +1674,23 @@ lb_status lb_set_state(lb_handle* h, const void* buf, size_t bytes) {
     if (!h || !buf || bytes < lb_state_bytes(h)) return fail(LB_EINVAL, "lb_set_state: bad buffer%s");
     StateHeader hd;
     std::memcpy(&hd, buf, sizeof hd);
-    if (hd.magic != kMagic || hd.planes != h->planes || hd.n_ch != h->n_ch || hd.nx != h->nx || hd.prec != h->prec ||
-        hd.smode != h->smode)
-        return fail(LB_EINVAL, "lb_set_state: image does not match this handle's grid%s");
+    if (hd.magic != kMagic || hd.version != kStateVersion)
+        return fail(LB_EINVAL, "lb_set_state: not a state image of this library version%s");
+    if (hd.planes != h->planes || hd.n_ch != h->n_ch || hd.nx != h->nx || hd.prec != h->prec ||
+        hd.smode != h->smode || hd.ny_hash != ny_list_hash(h->ny))
+        return fail(LB_EINVAL, "lb_set_state: image does not match this handle's grid or channel split%s");
     const char* p = (const char*)buf + sizeof hd;
     LB_CK(cudaMemcpyAsync(h->popA, p, 9 * h->planes * h->tsize, cudaMemcpyHostToDevice, h->stream));
     p += 9 * h->planes * h->tsize;
     LB_CK(cudaMemcpyAsync(h->drho, p, h->planes * h->csize, cudaMemcpyHostToDevice, h->stream));
     p += h->planes * h->csize;
     if (h->smode == 1) LB_CK(cudaMemcpyAsync(h->sig3, p, 3 * h->planes * h->csize, cudaMemcpyHostToDevice, h->stream));
+    // a restored state starts healthy: the per-channel status word and the sticky flags are
+    // cleared, so rolling back to a good image after an instability steps every channel again
+    LB_CK(cudaMemsetAsync(h->status_d, 0, sizeof(int) * h->n_ch, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
+    h->status_pending = false;
+    h->any_unstable = h->any_timeout = false;
     h->step = hd.step;
     h->uprev_state = -10;
     h->mon_state = -1;

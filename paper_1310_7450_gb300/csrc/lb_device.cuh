@@ -132,10 +132,11 @@ struct WorkItem {
 
 enum : int {
     F_FIELDS = 1,       // compute the fields of the state only (no population/state writes)
-    F_STORE_SIGMA = 2,  // write sigma (xx, yy, zz, xy) planes this step
+    F_STORE_SIGMA = 2,  // write the sigma xx, yy, xy planes this step (zz = 0 is written at create)
     F_SAVE_U = 4,       // write the reported velocity into the u_prev planes
     F_RESID = 8,        // accumulate the residual against u_prev (block partials)
     F_SR = 16,          // BF16 storage: stochastic rounding of the populations
+    F_MON = 32,         // accumulate flux and max |u| only (block partials; no u_prev read)
 };
 
 template <typename T, typename C>

@@ -16,8 +16,8 @@
 //   3. collision of row y: kappa by three-point differences from the velocity ring, the nlM
 //      stress, Sigma^nN, delta rho, n^eq, F_i (Eq. bodyforce), BGK; coalesced stores.
 // The periodic wrap of x is patched into the halo columns of the first and last strip with
-// plain loads.  Every mbarrier wait is bounded: on timeout the CTA records LB_ETIMEOUT in the
-// status word, drains its own copies (also bounded) and returns.
+// plain loads.  Every mbarrier wait is bounded (MarchCtl::max_wait_ns, 2 s by default): on timeout
+// the CTA records LB_ETIMEOUT in the status word, drains its own copies (also bounded) and returns.
 #pragma once
 
 #include <cuda.h>
@@ -36,7 +36,13 @@ struct MarchCtl {
     int* timeout_flag;  // the channel status word: bit 2 is set when a bounded wait gave up
     long long plane;    // plane stride of the channel's fields (elements)
     long long base;     // plane offset of the channel (its planes start at k * base)
+    unsigned long long max_wait_ns;  // limit of every mbarrier wait (0: one non-blocking probe)
 };
+
+// A CTA whose wait gave up waits this long for its own copies in flight before it returns.  A
+// bulk copy that has not landed after a second means the memory system has failed; the CTA
+// leaves then rather than spin without end.
+constexpr unsigned long long kMarchDrainNs = 1000000000ull;
 
 // ---- PTX helpers (mbarrier, TMA) ----------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -56,9 +62,20 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 // Bounded wait for the phase with the given parity: mbarrier.try_wait suspends the thread until
 // the phase completes or a hardware time limit passes; the loop gives up after max_ns of wall
-// time (returns false then).
+// time (returns false then).  max_ns = 0: a single non-blocking probe (mbarrier.test_wait).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t max_ns) {
     const uint32_t a = smem_u32(bar);
+    if (max_ns == 0) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        return done != 0;
+    }
     uint64_t t0 = 0;
     for (uint32_t k = 0;; ++k) {
         uint32_t done;
@@ -81,6 +98,10 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
+}
+// Bulk prefetch of bytes (a multiple of 16, 16-byte aligned) from global memory into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -110,7 +131,6 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
     constexpr int SW = W + 2 * HP;                                   // slot row width (elements)
     constexpr size_t SLOT = ((size_t)9 * SW * sizeof(T) + 127) / 128 * 128;
     constexpr uint32_t TX = 9u * SW * sizeof(T);                     // bytes per copy
-    constexpr uint64_t MAXWAIT = 2000000000ull;                      // bounded waits: 2 s
     constexpr int UW = W + 2;                                         // velocity ring row width
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -168,7 +188,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         auto idx_of = [&](int r) -> uint32_t { return L0 + (uint32_t)(r - rbase); };
         auto wait_row = [&](int r) -> bool {
             const uint32_t i = idx_of(r);
-            return mbar_wait(&bars[i % K], (i / K) & 1u, MAXWAIT);
+            return mbar_wait(&bars[i % K], (i / K) & 1u, ctl.max_wait_ns);
         };
         // periodic wrap: the edge strips' halo columns x0-2, x0-1 (left) or x0+W, x0+W+1 (right)
         // come from the other end of the row; threads 0..17 (left) and 32..49 (right) each own
@@ -283,7 +303,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         for (int r = rbase; r <= rbase + 5; ++r) ok &= wait_row(r);
         if (!ok) s_bad = 1;
         T pv_a = T(0), pv_b = T(0);
-        if (patcher) {
+        if (patcher && ok) {  // patch only slots whose copies this thread saw land
             for (int r = rbase; r <= rbase + 5; ++r) patch_store(r, patch_load(r));
             pv_a = patch_load(y0 + 4);
             pv_b = patch_load(y0 + 5);
@@ -299,10 +319,25 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         // the stored flow-induced density, loaded two rows ahead of its use
         C drho_next = a.drho[ctl.base + (long long)y0 * nx + x];
         C drho_next2 = (y0 + 1 < y1) ? a.drho[ctl.base + (long long)(y0 + 1) * nx + x] : C(0);
-        // on residual steps the saved velocity of each row is prefetched the same way
+        // on residual steps the saved velocity of each row is prefetched the same way, and one
+        // thread brings the delta rho and saved-velocity rows into L2 four rows before their
+        // register loads (a residual step reads 16 B more per node than a plain one, and the
+        // two-rows-ahead register pipeline alone covers about one row of DRAM latency)
         const bool resid = (a.flags & F_RESID) != 0;
+        const bool mon = (a.flags & (F_RESID | F_MON)) != 0;
         const C* upx = a.uprev + 2 * ctl.base + x;
         const C* upy = upx + ctl.plane;
+        constexpr int TP = 32;  // the thread that issues the L2 prefetches (lane 0 of warp 1)
+        auto prefetch_rows = [&](int r) {  // thread TP, residual steps, rows of this item only
+            if (r < y1) {
+                const long long o = (long long)r * nx + x0;
+                prefetch_l2(a.drho + ctl.base + o, W * sizeof(C));
+                prefetch_l2(a.uprev + 2 * ctl.base + o, W * sizeof(C));
+                prefetch_l2(a.uprev + 2 * ctl.base + ctl.plane + o, W * sizeof(C));
+            }
+        };
+        if (resid && t == TP)
+            for (int r = y0 + 2; r < y0 + 6; ++r) prefetch_rows(r);
         C upx_next = C(0), upy_next = C(0), upx_next2 = C(0), upy_next2 = C(0);
         if (resid) {
             upx_next = upx[(long long)y0 * nx];
@@ -324,7 +359,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             if (y + 2 <= rlast && !wait_row(y + 2)) s_bad = 1;
             if (patcher && y + 4 <= rlast) {
                 if (!wait_row(y + 4)) s_bad = 1;
-                patch_store(y + 4, pv_a);
+                else patch_store(y + 4, pv_a);
                 pv_a = pv_b;
                 pv_b = patch_load(y + 6);
             }
@@ -334,6 +369,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             if (y + 2 < y1) drho_next2 = a.drho[ctl.base + (long long)(y + 2) * nx + x];
             const C upx_cur = upx_next, upy_cur = upy_next;
             if (resid) {
+                if (t == TP) prefetch_rows(y + 6);
                 upx_next = upx_next2;
                 upy_next = upy_next2;
                 if (y + 2 < y1) {
@@ -390,21 +426,22 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                     s3[ctl.plane + pn] = s.sxy;
                     s3[2 * ctl.plane + pn] = s.syy;
                 }
-                if (a.flags & F_STORE_SIGMA) {
+                if (a.flags & F_STORE_SIGMA) {  // (the zz plane holds 0 from lb_create on)
                     C* s4 = a.sig4 + 4 * ctl.base;
                     s4[pn] = s.sxx;
                     s4[ctl.plane + pn] = s.syy;
-                    s4[2 * ctl.plane + pn] = C(0);
                     s4[3 * ctl.plane + pn] = s.sxy;
                 }
-                if (a.flags & (F_SAVE_U | F_RESID)) {
+                if (a.flags & (F_SAVE_U | F_RESID | F_MON)) {
                     const C ih = Arith<C>::div(C(1), rho_h);
                     const C urx = jxc * ih, ury = jyc * ih;
                     C* up_ = a.uprev + 2 * ctl.base;
-                    if (a.flags & F_RESID) {
-                        const C dx_ = urx - upx_cur, dy_ = ury - upy_cur;
+                    if (mon) {
                         const C u2 = urx * urx + ury * ury;
-                        r_du2 += dx_ * dx_ + dy_ * dy_;
+                        if (resid) {
+                            const C dx_ = urx - upx_cur, dy_ = ury - upy_cur;
+                            r_du2 += dx_ * dx_ + dy_ * dy_;
+                        }
                         r_u2 += u2;
                         r_ux += urx;
                         r_umax2 = fmax(r_umax2, u2);
@@ -420,7 +457,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             dRc = dRn; jxc = jxn; jyc = jyn;
         }
         __syncthreads();  // every slot read of this item is done before the next item's copies
-        if (!bad && (a.flags & F_RESID)) {
+        if (!bad && mon) {
             // block reduction of (sum du^2, sum u^2, sum u_x, max |u|) into this item's partials
             double v[4] = {(double)r_du2, (double)r_u2, (double)r_ux, (double)r_umax2};
 #pragma unroll
@@ -448,11 +485,13 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
 
     if (vbad) atomicOr(a.status, 1);
     if (bad) {
-        // record the timeout and drain this CTA's own copies (bounded) before leaving
+        // record the timeout and drain this CTA's own copies before leaving: a slot is refilled
+        // only after every thread's wait on its previous copy succeeded, so the last copy issued
+        // into each slot is the only one that can still be in flight (bounded by kMarchDrainNs)
         if (t == TI) {
             atomicOr(ctl.timeout_flag, 2);
             for (int k = 0; k < K; ++k)
-                if (last_issued[k] != 0xffffffffu) mbar_wait(&bars[k], (last_issued[k] / K) & 1u, 100000000ull);
+                if (last_issued[k] != 0xffffffffu) mbar_wait(&bars[k], (last_issued[k] / K) & 1u, kMarchDrainNs);
         }
         __syncthreads();
     }

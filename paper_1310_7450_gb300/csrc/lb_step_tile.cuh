@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
         const C rho_h = C(1) + s.dReq - s.drho;
         if (!velocity_ok<C>(jx, jy, rho_h, a.guard)) atomicOr(a.status + it.ch, 1);  // NaN or too fast
         C urx = C(0), ury = C(0);
-        if (a.flags & (F_FIELDS | F_SAVE_U | F_RESID)) {
+        if (a.flags & (F_FIELDS | F_SAVE_U | F_RESID | F_MON)) {
             const C ih = Arith<C>::div(C(1), rho_h);
             urx = jx * ih;
             ury = jy * ih;
@@ -199,19 +199,20 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
                 s3[P.P + pn] = s.sxy;
                 s3[2 * P.P + pn] = s.syy;
             }
-            if (a.flags & F_STORE_SIGMA) {
+            if (a.flags & F_STORE_SIGMA) {  // (the zz plane holds 0 from lb_create on)
                 C* s4 = a.sig4 + 4 * P.base;
                 s4[pn] = s.sxx;
                 s4[P.P + pn] = s.syy;
-                s4[2 * P.P + pn] = C(0);
                 s4[3 * P.P + pn] = s.sxy;
             }
         }
-        if (a.flags & (F_RESID | F_SAVE_U)) {
+        if (a.flags & (F_RESID | F_SAVE_U | F_MON)) {
             C* up = a.uprev + 2 * P.base;
-            if (a.flags & F_RESID) {
-                const C dx_ = urx - up[pn], dy_ = ury - up[P.P + pn];
-                res_du2 = dx_ * dx_ + dy_ * dy_;
+            if (a.flags & (F_RESID | F_MON)) {
+                if (a.flags & F_RESID) {
+                    const C dx_ = urx - up[pn], dy_ = ury - up[P.P + pn];
+                    res_du2 = dx_ * dx_ + dy_ * dy_;
+                }
                 res_u2 = urx * urx + ury * ury;
                 res_ux = urx;
                 res_umax = Arith<C>::sqrt(res_u2);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
             }
         }
     }
-    if (a.flags & F_RESID) {
+    if (a.flags & (F_RESID | F_MON)) {
         // block reduction of (sum du^2, sum u^2, sum u_x, max |u|) in double
         __shared__ double red[NT / 32][4];
         double v0 = warp_sum<double>((double)res_du2), v1 = warp_sum<double>((double)res_u2);

@@ -25,6 +25,7 @@ LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY, LB_GRID_BF16_STOCHASTIC, LB_GRID_NO_GRAP
 LB_X_PERIODIC, LB_X_GPBC = 1, 2
 X_MODES = {"periodic": LB_X_PERIODIC, "gpbc": LB_X_GPBC}
 LB_WALLS_BOUNCE_BACK, LB_WALLS_COUETTE = 1, 2
+LB_MONITOR_RESIDUAL, LB_MONITOR_FLUX_MAX = 0, 1
 WALLS = {"bounce_back": LB_WALLS_BOUNCE_BACK, "couette": LB_WALLS_COUETTE}
 LB_PREC_F64S_F32M, LB_PREC_F32S_F64M = 3, 4
 PRECISIONS = {"f64": LB_PREC_F64, "f32": LB_PREC_F32, "bf16": LB_PREC_BF16, "f64s_f32m": LB_PREC_F64S_F32M,
@@ -81,6 +82,8 @@ def load():
         "lb_get_state": ([_H, c_void_p, c_size_t], c_int),
         "lb_set_state": ([_H, c_void_p, c_size_t], c_int),
         "lb_channel_status": ([_H, POINTER(c_int)], c_int),
+        "lb_set_wait_limit": ([_H, c_double], c_int),
+        "lb_set_monitor_mode": ([_H, c_int], c_int),
         "lb_step_count": ([_H], c_long),
         "lb_mlp_create": ([c_int, c_int, c_int, c_int, c_uint64, c_void_p, POINTER(c_void_p)], c_int),
         "lb_mlp_destroy": ([_H], None),
@@ -218,6 +221,14 @@ def lb_get_state(h: int, buf: np.ndarray):
 
 def lb_set_state(h: int, buf: np.ndarray):
     _check(load().lb_set_state(h, c_void_p(buf.ctypes.data), buf.nbytes), "lb_set_state")
+
+
+def lb_set_monitor_mode(h: int, mode: int):
+    _check(load().lb_set_monitor_mode(h, int(mode)), "lb_set_monitor_mode")
+
+
+def lb_set_wait_limit(h: int, seconds: float):
+    _check(load().lb_set_wait_limit(h, float(seconds)), "lb_set_wait_limit")
 
 
 def lb_channel_status(h: int, out: np.ndarray):

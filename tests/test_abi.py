@@ -104,3 +104,14 @@ def test_no_cpu_fallback_without_a_gpu(lib):
         lbnlm.lb_create(4, 16, p, 0, 0)
     assert e.value.status == lbnlm.LB_ECUDA
     assert "lb_create" in lbnlm.lb_last_error()
+
+
+def test_wait_limit_validation_before_device_work(lib):
+    """lb_set_wait_limit rejects a null handle before touching the device."""
+    from paper_1310_7450_gb300 import lbnlm
+    assert lib.lb_set_wait_limit(None, 1.0) == lbnlm.LB_EINVAL
+
+
+def test_monitor_mode_validation_before_device_work(lib):
+    from paper_1310_7450_gb300 import lbnlm
+    assert lib.lb_set_monitor_mode(None, lbnlm.LB_MONITOR_FLUX_MAX) == lbnlm.LB_EINVAL

@@ -21,11 +21,11 @@ def load_bench():
 @pytest.mark.parametrize("prec,sigma,mode,expected", [
     # 9 loads + 9 stores of the storage type, delta rho read + write in the arithmetic type
     ("f32", False, 0, 18 * 4 + 2 * 4),
-    ("f32", True, 0, 96),            # + the 4-component stress written every step
+    ("f32", True, 0, 92),            # + the stress xx, yy, xy written every step (zz = 0 once)
     ("bf16", False, 0, 18 * 2 + 2 * 4),
-    ("bf16", True, 0, 60),
-    ("f64", True, 0, 18 * 8 + 2 * 8 + 4 * 8),
-    ("f32", True, 1, 96 + 6 * 4),    # mode B: the carried (xx, xy, yy) stress read and written
+    ("bf16", True, 0, 56),
+    ("f64", True, 0, 18 * 8 + 2 * 8 + 3 * 8),
+    ("f32", True, 1, 92 + 6 * 4),    # mode B: the carried (xx, xy, yy) stress read and written
 ])
 def test_bytes_per_node(prec, sigma, mode, expected):
     assert load_bench().bytes_per_node(prec, sigma, mode) == expected

@@ -225,6 +225,112 @@ def test_checkpoint_resume_bitwise(stream, prec):
     assert np.array_equal(na, nb) and np.array_equal(da, db)
 
 
+def test_checkpoint_rejects_other_channel_split_and_version(stream):
+    """An image of channels [24, 40] does not load into a handle of [40, 24] (same planes, same
+    node count), nor an image whose version field was altered."""
+    p = dict(nlm(), rho_pert_amp=1e-3, seed=4)
+    with lbnlm.Channels(4, [24, 40], [p, p], "f32", stream=stream) as a, \
+            lbnlm.Channels(4, [40, 24], [p, p], "f32", stream=stream) as b:
+        a.step(3)
+        buf = np.zeros(lbnlm.lb_state_bytes(a.h), dtype=np.uint8)
+        assert buf.nbytes == lbnlm.lb_state_bytes(b.h)
+        lbnlm.lb_get_state(a.h, buf)
+        with pytest.raises(lbnlm.LBError) as e:
+            lbnlm.lb_set_state(b.h, buf)
+        assert e.value.status == lbnlm.LB_EINVAL and "channel split" in lbnlm.lb_last_error()
+        bad = buf.copy()
+        bad[8] ^= 0x7f                      # the version field follows the 8-byte magic
+        with pytest.raises(lbnlm.LBError) as e:
+            lbnlm.lb_set_state(a.h, bad)
+        assert e.value.status == lbnlm.LB_EINVAL and "version" in lbnlm.lb_last_error()
+        lbnlm.lb_set_state(a.h, buf)        # the untouched image still loads
+
+
+def test_rollback_after_instability_steps_every_channel_again(stream):
+    """A checkpoint taken before a host-side NaN injection, restored after the channel was retired,
+    clears the status: every channel steps again and the result equals an uninterrupted run."""
+    nys = [12, 12, 12]
+    ps = [dict(nlm(), rho_pert_amp=1e-3, seed=s) for s in (1, 2, 3)]
+    with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim, \
+            lbnlm.Channels(4, nys, ps, "f64", stream=stream) as ref:
+        sim.step(10)
+        buf = np.zeros(lbnlm.lb_state_bytes(sim.h), dtype=np.uint8)
+        lbnlm.lb_get_state(sim.h, buf)
+        pops = sim.populations()
+        n1 = pops[1][0].copy()
+        n1[3, 5, 2] = np.nan
+        sim.set_populations([pops[0][0], n1, pops[2][0]], [pops[0][1], pops[1][1], pops[2][1]])
+        sim.step(5)
+        assert list(sim.status()) == [0, 1, 0]     # (synchronous read of the status word)
+        assert sim.step(1) == lbnlm.LB_EUNSTABLE
+        lbnlm.lb_set_state(sim.h, buf)
+        assert list(sim.status()) == [0, 0, 0]
+        assert sim.step(20) == lbnlm.LB_OK
+        ref.step(30)
+        got, want = sim.populations(), ref.populations()
+    for (ng, dg), (nw, dw) in zip(got, want):
+        assert np.array_equal(ng, nw) and np.array_equal(dg, dw)
+
+
+@pytest.mark.parametrize("case", ["row_march_f32", "tile_f64_channels"])
+def test_flux_max_monitor_mode(stream, case):
+    """LB_MONITOR_FLUX_MAX: the last step of each call forms flux and max |u| from its own state
+    without the saved velocity.  They equal, bitwise, those of the residual mode on the same state;
+    the residual slot reads -1 and lb_residual refuses; the populations do not depend on the mode."""
+    if case == "row_march_f32":
+        nx, nys, prec = 256, [64], "f32"
+    else:
+        nx, nys, prec = 6, [11, 17], "f64"
+    ps = [dict(nlm(), rho_pert_amp=1e-3, seed=20 + k) for k in range(len(nys))]
+    with lbnlm.Channels(nx, nys, ps, prec, stream=stream) as a, lbnlm.Channels(nx, nys, ps, prec, stream=stream) as b:
+        assert bool(lbnlm.lb_uses_row_march(a.h)) == (case == "row_march_f32")
+        lbnlm.lb_set_monitor_mode(b.h, lbnlm.LB_MONITOR_FLUX_MAX)
+        for n in (5, 1, 3):
+            a.step(n)
+            b.step(n)
+            ma, mb = a.monitor(), b.monitor()
+            assert np.all(np.isfinite(ma[:, 0])) and np.all(mb[:, 0] == -1.0)
+            assert np.array_equal(ma[:, 1:], mb[:, 1:])
+        with pytest.raises(lbnlm.LBError) as e:
+            lbnlm.lb_residual(b.h, np.zeros(len(nys)))
+        assert e.value.status == lbnlm.LB_ESTATE
+        pa, pb = a.populations(), b.populations()
+    for (na, da), (nb, db) in zip(pa, pb):
+        assert np.array_equal(na, nb) and np.array_equal(da, db)
+
+
+def test_row_march_wait_limit_reports_timeout_and_recovers(stream):
+    """The row-march kernel's bounded mbarrier waits: with the limit at 0 (one non-blocking probe,
+    while a fresh row copy takes far longer than the probe) a wait gives up, the CTA drains its own
+    copies and returns, status bit 2 is set and the next lb_step reports LB_ETIMEOUT.  Restoring a
+    checkpoint clears the status; with the default limit the handle steps on bit-for-bit like an
+    untouched one."""
+    nx, ny = 256, 64
+    p = dict(nlm(), rho_pert_amp=1e-3, seed=12)
+    with lbnlm.Channels(nx, ny, p, "f32", stream=stream) as sim, \
+            lbnlm.Channels(nx, ny, p, "f32", stream=stream) as ref:
+        assert lbnlm.lb_uses_row_march(sim.h)
+        sim.step(4)
+        buf = np.zeros(lbnlm.lb_state_bytes(sim.h), dtype=np.uint8)
+        lbnlm.lb_get_state(sim.h, buf)
+        lbnlm.lb_set_wait_limit(sim.h, 0.0)
+        sim.step(1)
+        assert list(sim.status()) == [2]
+        with pytest.raises(lbnlm.LBError) as e:
+            sim.step(1)
+        assert e.value.status == lbnlm.LB_ETIMEOUT
+        lbnlm.lb_set_wait_limit(sim.h, 2.0)
+        lbnlm.lb_set_state(sim.h, buf)
+        assert list(sim.status()) == [0]
+        assert sim.step(6) == lbnlm.LB_OK
+        ref.step(10)
+        (ng, dg), = sim.populations()
+        (nw, dw), = ref.populations()
+    assert np.array_equal(ng, nw) and np.array_equal(dg, dw)
+    with pytest.raises(lbnlm.LBError):
+        lbnlm.lb_set_wait_limit(0, 1.0)
+
+
 def test_unstable_channel_is_retired_and_others_unaffected(stream):
     nys = [12, 12, 12]
     ps = [dict(nlm(), rho_pert_amp=1e-3, seed=s) for s in (1, 2, 3)]
