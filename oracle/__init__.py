@@ -29,6 +29,12 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                      continuity of the mass flux, equality with the body-force run (Sec. II B)
     Couette runs     pinned: brute-force twin, exact linear Newtonian profile, start-up Fourier
                      series, homogeneous nlM shear (Sec. III A closed forms), mass invariance
+    comparison       generalized-Newtonian scheme: steady channel against Eq. (maxwellpoiseuille)
+    schemes          with second-order convergence, theta = 0 equal to the paper's scheme, no
+    (Sec. II C)      normal stresses; stress-divergence scheme: steady channel against the
+                     paper's scheme to O(H^-2) and against Eq. (maxwellpoiseuille), Newtonian
+                     cross-check (a Delta eta D stress acts as the viscosity Delta eta)
+                     (tests/test_oracle_schemes.py)
 """
 from __future__ import annotations
 
@@ -60,7 +66,10 @@ class OrcParams(ctypes.Structure):
                 ("tau0", ctypes.c_double), ("theta", ctypes.c_double), ("gamma_c", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("stress_mode", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double), ("top_wall", ctypes.c_int),
-                ("pad_", ctypes.c_int), ("u_wall", ctypes.c_double)]
+                ("scheme", ctypes.c_int), ("u_wall", ctypes.c_double)]
+
+
+SCHEMES = {"paper": 0, "generalized_newtonian": 1, "stress_divergence": 2}
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -122,14 +131,16 @@ def to_params(p, nx: int | None = None) -> OrcParams:
     """Accepts a mapping (or object) with tau_lb, g_x, G_inf, tau0, theta, gamma_c, rho0,
     stress_mode and optionally x_mode ("periodic" or "gpbc"; GPBC needs nx), top_wall
     ("bounce_back" or "moving": planar Couette flow with a Zou-He wall on the last row) and
-    u_wall."""
+    u_wall; scheme ("paper", "generalized_newtonian" or "stress_divergence", the comparison
+    schemes of Sec. II C)."""
     get = (lambda k, d=None: p.get(k, d)) if isinstance(p, dict) else (lambda k, d=None: getattr(p, k, d))
     gpbc = get("x_mode", "periodic") == "gpbc"
     rin, rout = gpbc_density_offsets(p, nx) if gpbc else (0.0, 0.0)
     return OrcParams(float(get("tau_lb")), float(get("g_x", 0.0)), float(get("G_inf", 0.0)),
                      float(get("tau0", 0.0)), float(get("theta", 0.0)), float(get("gamma_c", np.inf)),
                      float(get("rho0", 1.0)), int(get("stress_mode", 0)), 1 if gpbc else 0, rin, rout,
-                     1 if get("top_wall", "bounce_back") == "moving" else 0, 0, float(get("u_wall", 0.0)))
+                     1 if get("top_wall", "bounce_back") == "moving" else 0,
+                     SCHEMES[get("scheme", "paper")], float(get("u_wall", 0.0)))
 
 
 # --- per-node functions ---------------------------------------------------------------------
@@ -269,9 +280,9 @@ def fields(params, st: State):
 
 
 def intermediates(params, st: State) -> np.ndarray:
-    """[ny, nx, 8]: kxx, kxy, kyx, kyy, tau_M, drho, S, rho_eq of the next update."""
+    """[ny, nx, 9]: kxx, kxy, kyx, kyy, tau_M, drho, S, rho_eq, tau_LB of the next update."""
     ny, nx = st.shape
-    out = np.zeros((ny, nx, 8))
+    out = np.zeros((ny, nx, 9))
     pp = to_params(params, nx)
     rc = _load().orc_node_intermediates(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho),
                                         _p(st.sig), _p(out))

@@ -59,6 +59,21 @@
  * bounce-back of its non-equilibrium part, the two diagonal ones from the wall's tangential
  * momentum.  The bottom wall stays the half-way bounce-back wall at y = -1/2, so the gap is
  * ny - 1/2.
+ *
+ * Comparison schemes (Sec. II C lists them as the usual alternatives to the paper's forcing;
+ * scheme = 1, 2; periodic x, bounce-back walls and stress mode 0 only):
+ *   scheme 1, generalized Newtonian: tau_LB follows Eq. (taulb) with the Newtonian viscosity
+ *     replaced by the effective viscosity of the model in steady shear, eta_eff = G tau_M +
+ *     eta_inf (tau_M of Eq. nlmaxwell at the node's shear rate), and F_i keeps only its body-force
+ *     terms: no stress line, no flow-induced density.  The stress reported is G tau_M D (such a
+ *     fluid has no normal-stress differences).
+ *   scheme 2, divergence of the stress as a body force: the stress enters as the force density
+ *     f^nN = div Sigma^nN (three-point differences as for kappa) instead of the stress line and
+ *     the flow-induced density.  Explicit order as for the paper's scheme: kappa from j / R0 with
+ *     j = J0 + f^ex/2, then sigma and Sigma^nN at every node, their divergence, then
+ *     j = J0 + (f^ex + f^nN)/2 for n^eq and the force terms of Eq. (bodyforce) with f^ex + f^nN.
+ *     (A divergence lagged by one step went unstable once Sigma^nN acted as a negative viscosity
+ *     beyond -0.3 eta^N, and oscillated from step to step near tau_LB = 1/2.)
  */
 #include <math.h>
 #include <stdint.h>
@@ -92,7 +107,7 @@ typedef struct {
                        as an offset from 1 like the populations                              */
     double rho_out; /* GPBC: c_s^-2 p_- - 1 at the outlet (x = nx)                            */
     int top_wall;   /* 0: half-way bounce-back; 1: wall on row ny-1 moving with u_wall (Zou-He) */
-    int pad_;
+    int scheme;     /* 0: the paper's forcing; 1: generalized Newtonian tau_LB; 2: div Sigma force */
     double u_wall;  /* tangential velocity of the moving wall                                   */
 } orc_params;
 
@@ -340,6 +355,8 @@ typedef struct {
     double sbar[3];        /* traceless part of Sigma^nN (xx, xy, yy)                 */
     double drho, S;        /* delta rho(t) and S = delta rho(t) - delta rho(t-1)       */
     double rho_eq_m1, u[2];/* density (minus 1) and velocity handed to n^eq           */
+    double tau_lb;         /* relaxation time of this node's collision                */
+    double snn[3];         /* Sigma^nN (xx, xy, yy)                                   */
 } node_result;
 
 static inline long idx(int nx, int x, int y) { return (long)y * nx + x; }
@@ -358,6 +375,29 @@ static double ddy(const double *v, int nx, int ny, int x, int y, int comp) {
 static double ddx(const double *v, int nx, int x, int y, int comp) {
     int xp = (x + 1) % nx, xm = (x - 1 + nx) % nx;
     return 0.5 * (v[2 * idx(nx, xp, y) + comp] - v[2 * idx(nx, xm, y) + comp]);
+}
+
+/* The same three-point differences of a scalar field f[y][x] (scheme 2: the stress planes). */
+static double plane_ddy(const double *f, int nx, int ny, int x, int y) {
+    if (y == 0) return 0.5 * (-3.0 * f[idx(nx, x, 0)] + 4.0 * f[idx(nx, x, 1)] - f[idx(nx, x, 2)]);
+    if (y == ny - 1) return 0.5 * (3.0 * f[idx(nx, x, ny - 1)] - 4.0 * f[idx(nx, x, ny - 2)] + f[idx(nx, x, ny - 3)]);
+    return 0.5 * (f[idx(nx, x, y + 1)] - f[idx(nx, x, y - 1)]);
+}
+static double plane_ddx(const double *f, int nx, int x, int y) {
+    int xp = (x + 1) % nx, xm = (x - 1 + nx) % nx;
+    return 0.5 * (f[idx(nx, xp, y)] - f[idx(nx, xm, y)]);
+}
+
+/* Scheme 2: f^nN_a = d_b Sigma^nN_ab of the stored stress planes snn = (xx, xy, yy); out [2][N]. */
+static void stress_divergence(int nx, int ny, const double *snn, double *out) {
+    long N = (long)nx * ny;
+    const double *sxx = snn, *sxy = snn + N, *syy = snn + 2 * N;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            long k = idx(nx, x, y);
+            out[k] = plane_ddx(sxx, nx, x, y) + plane_ddy(sxy, nx, ny, x, y);
+            out[N + k] = plane_ddx(sxy, nx, x, y) + plane_ddy(syy, nx, ny, x, y);
+        }
 }
 
 /* Steps 3-6 of the header, and the density / velocity of step 7, for node (x,y): needs the
@@ -380,6 +420,24 @@ static void node_update(const orc_params *p, int nx, int ny, int x, int y,
         for (int b = 0; b < 2; ++b) II_D += 0.5 * D[a][b] * D[b][a];
     double tau = p->theta * p->tau0;
     r->tau_M = orc_relaxation_time(tau, p->gamma_c, II_D);
+    r->tau_lb = p->tau_lb;
+    if (p->scheme == 1) {
+        /* generalized Newtonian: a locally Newtonian fluid with the effective viscosity of the
+         * model in steady shear, eta_eff = G tau_M + eta_inf, through Eq. (taulb):
+         * tau_LB = 1/2 + eta_eff / (rho0 c_s^2); the stress is G tau_M D, F_i has no stress line */
+        r->sigma[0] = p->G_inf * r->tau_M * D[0][0];
+        r->sigma[1] = p->G_inf * r->tau_M * D[0][1];
+        r->sigma[2] = p->G_inf * r->tau_M * D[1][1];
+        double eta_eff = p->G_inf * r->tau_M + p->G_inf * p->tau0;
+        r->tau_lb = 0.5 + eta_eff / (p->rho0 * ORC_CS2);
+        r->sbar[0] = r->sbar[1] = r->sbar[2] = 0.0;
+        r->snn[0] = r->snn[1] = r->snn[2] = 0.0;
+        r->drho = r->S = 0.0;
+        r->rho_eq_m1 = r->R0m1;
+        r->u[0] = r->j[0] / (1.0 + r->rho_eq_m1);
+        r->u[1] = r->j[1] / (1.0 + r->rho_eq_m1);
+        return;
+    }
     if (p->stress_mode == 0) {
         if (orc_stress_series(r->kap, r->tau_M, p->G_inf, r->sigma) < 0) {
             orc_stress_gauss(r->kap, r->tau_M, p->G_inf, r->sigma);
@@ -406,12 +464,21 @@ static void node_update(const orc_params *p, int nx, int ny, int x, int y,
     double nn_xy = r->sigma[1] + (eta_inf - eta_N) * D[0][1];
     double nn_yy = r->sigma[2] + (eta_inf - eta_N) * D[1][1];
     double trace = nn_xx + nn_yy;
+    r->snn[0] = nn_xx;
+    r->snn[1] = nn_xy;
+    r->snn[2] = nn_yy;
     r->sbar[0] = nn_xx - trace / ORC_DIM;     /* overbar: traceless part (Sec. II A)     */
     r->sbar[1] = nn_xy;
     r->sbar[2] = nn_yy - trace / ORC_DIM;
     r->drho = -trace / (ORC_CS2 * ORC_DIM);   /* flow-induced density change (Sec. II A) */
     r->S = r->drho - drho_prev[k];            /* dt d_t delta rho, Eq. (rhoplus)         */
     if (p->boundary == 1) r->drho = r->S = 0.0; /* GPBC: no density correction (Sec. II B) */
+    if (p->scheme == 2) {
+        /* the stress acts through its divergence (a force density, in j and the force terms
+         * of Eq. bodyforce) instead of the stress line and the flow-induced density */
+        r->sbar[0] = r->sbar[1] = r->sbar[2] = 0.0;
+        r->drho = r->S = 0.0;
+    }
     /* reading: sum_i n^eq = sum_i (n* + n)/2 = R0 + S/2, so that sum_i (Delta_i + F_i) = S */
     r->rho_eq_m1 = r->R0m1 + 0.5 * r->S;
     r->u[0] = r->j[0] / (1.0 + r->rho_eq_m1);
@@ -531,7 +598,7 @@ static void stream_and_moments(const orc_params *p, int nx, int ny, const double
 }
 
 typedef struct {
-    double *n, *R0m1, *j, *ug;
+    double *n, *R0m1, *j, *ug, *fnn, *snn;
 } orc_work;
 
 static int work_alloc(orc_work *w, long N) {
@@ -539,17 +606,62 @@ static int work_alloc(orc_work *w, long N) {
     w->R0m1 = (double *)malloc(sizeof(double) * N);
     w->j = (double *)malloc(sizeof(double) * 2 * N);
     w->ug = (double *)malloc(sizeof(double) * 2 * N);
-    return (w->n && w->R0m1 && w->j && w->ug) ? 0 : -1;
+    w->fnn = (double *)malloc(sizeof(double) * 2 * N);
+    w->snn = (double *)malloc(sizeof(double) * 3 * N);
+    return (w->n && w->R0m1 && w->j && w->ug && w->fnn && w->snn) ? 0 : -1;
 }
-static void work_free(orc_work *w) { free(w->n); free(w->R0m1); free(w->j); free(w->ug); }
+static void work_free(orc_work *w) {
+    free(w->n); free(w->R0m1); free(w->j); free(w->ug); free(w->fnn); free(w->snn);
+}
 
 static int valid_grid(int nx, int ny) { return nx >= 1 && ny >= 3; }
+
+/* The comparison schemes run with periodic x, bounce-back walls and stress mode 0. */
+static int valid_scheme(const orc_params *p) {
+    if (p->scheme == 0) return 1;
+    if (p->scheme != 1 && p->scheme != 2) return 0;
+    return p->stress_mode == 0 && p->boundary == 0 && p->top_wall == 0;
+}
+
+/* Moments of the streamed state.  Scheme 2 then needs the stress of every node before any node
+ * can collide (explicit order, as for the paper's scheme: kappa from j / R0 with j = J0 + f^ex/2;
+ * sigma and Sigma^nN; their divergence f^nN; then j = J0 + (f^ex + f^nN)/2 for n^eq and F_i):
+ * w->fnn receives f^nN [2][N], and j and ug are not changed by it. */
+static void moments_for_step(const orc_params *p, int nx, int ny, const double *dn_star, const double *drho,
+                             const double *sig, orc_work *w) {
+    stream_and_moments(p, nx, ny, dn_star, w->n, w->R0m1, w->j, w->ug);
+    if (p->scheme != 2) return;
+    long N = (long)nx * ny;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            long k = idx(nx, x, y);
+            node_result r;
+            node_update(p, nx, ny, x, y, w->R0m1, w->j, w->ug, drho, sig, &r);
+            w->snn[k] = r.snn[0];
+            w->snn[N + k] = r.snn[1];
+            w->snn[2 * N + k] = r.snn[2];
+        }
+    stress_divergence(nx, ny, w->snn, w->fnn);
+}
+
+/* Scheme 2: the node's force density f^ex + f^nN, and j, u of Eq. (rhoj) / Eq. (neq) with it. */
+static void stress_force(const orc_params *p, const orc_work *w, long N, long k, node_result *r, double *f) {
+    f[0] = body_force(p);
+    f[1] = 0.0;
+    if (p->scheme != 2) return;
+    f[0] += w->fnn[k];
+    f[1] += w->fnn[N + k];
+    r->j[0] += 0.5 * w->fnn[k];
+    r->j[1] += 0.5 * w->fnn[N + k];
+    r->u[0] = r->j[0] / (1.0 + r->rho_eq_m1);
+    r->u[1] = r->j[1] / (1.0 + r->rho_eq_m1);
+}
 
 /* Advance the state (dn_star, drho, sig) by nsteps steps in place.  Returns 0, or -1 on a bad
  * argument / allocation failure. */
 int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, double *sig,
             long nsteps, int nthreads) {
-    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig)) return -1;
+    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p)) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -559,7 +671,7 @@ int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, 
     orc_work w;
     if (work_alloc(&w, N)) { work_free(&w); return -1; }
     for (long s = 0; s < nsteps; ++s) {
-        stream_and_moments(p, nx, ny, dn_star, w.n, w.R0m1, w.j, w.ug);
+        moments_for_step(p, nx, ny, dn_star, drho, sig, &w);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
 #endif
@@ -568,14 +680,14 @@ int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, 
                 long k = idx(nx, x, y);
                 node_result r;
                 node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
-                double dneq[9], F[9];
+                double dneq[9], F[9], f[2];
+                stress_force(p, &w, N, k, &r, f);
                 orc_equilibrium_offset(r.rho_eq_m1, r.u[0], r.u[1], dneq);
-                double f[2] = {body_force(p), 0.0};
-                orc_forcing(p->tau_lb, r.sbar, r.S, r.u, f, F);
+                orc_forcing(r.tau_lb, r.sbar, r.S, r.u, f, F);
                 for (int i = 0; i < 9; ++i) {
                     /* BGK: n* = n - (n - n^eq)/tau_LB + F, on offsets from w_i */
                     double dni = w.n[i * N + k];
-                    dn_star[i * N + k] = dni - (dni - dneq[i]) / p->tau_lb + F[i];
+                    dn_star[i * N + k] = dni - (dni - dneq[i]) / r.tau_lb + F[i];
                 }
                 drho[k] = r.drho;
                 if (p->stress_mode == 1) {
@@ -583,6 +695,7 @@ int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, 
                     sig[N + k] = r.sigma[1];
                     sig[2 * N + k] = r.sigma[2];
                 }
+
             }
     }
     work_free(&w);
@@ -596,16 +709,18 @@ int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, 
  * The state is not modified. */
 int orc_fields(const orc_params *p, int nx, int ny, const double *dn_star, const double *drho,
                const double *sig, double *u, double *sigma, double *rho) {
-    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig)) return -1;
+    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p)) return -1;
     long N = (long)nx * ny;
     orc_work w;
     if (work_alloc(&w, N)) { work_free(&w); return -1; }
-    stream_and_moments(p, nx, ny, dn_star, w.n, w.R0m1, w.j, w.ug);
+    moments_for_step(p, nx, ny, dn_star, drho, sig, &w);
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(nx, x, y);
             node_result r;
+            double f[2];
             node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
+            stress_force(p, &w, N, k, &r, f);
             double rho_h = 1.0 + (r.rho_eq_m1 - r.drho);
             if (u) { u[2 * k] = r.j[0] / rho_h; u[2 * k + 1] = r.j[1] / rho_h; }
             if (sigma) {
@@ -621,22 +736,24 @@ int orc_fields(const orc_params *p, int nx, int ny, const double *dn_star, const
 }
 
 /* Diagnostic access to the per-node intermediates of one update (kappa, tau_M, drho, S),
- * used by tests: out[y][x][8] = kxx, kxy, kyx, kyy, tau_M, drho, S, rho_eq. */
+ * used by tests: out[y][x][9] = kxx, kxy, kyx, kyy, tau_M, drho, S, rho_eq, tau_LB of the node. */
 int orc_node_intermediates(const orc_params *p, int nx, int ny, const double *dn_star,
                            const double *drho, const double *sig, double *out) {
-    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig)) return -1;
+    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p)) return -1;
     long N = (long)nx * ny;
     orc_work w;
     if (work_alloc(&w, N)) { work_free(&w); return -1; }
-    stream_and_moments(p, nx, ny, dn_star, w.n, w.R0m1, w.j, w.ug);
+    moments_for_step(p, nx, ny, dn_star, drho, sig, &w);
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(nx, x, y);
             node_result r;
+            double f[2];
             node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
-            double *o = out + 8 * k;
+            stress_force(p, &w, N, k, &r, f);
+            double *o = out + 9 * k;
             o[0] = r.kap[0]; o[1] = r.kap[1]; o[2] = r.kap[2]; o[3] = r.kap[3];
-            o[4] = r.tau_M; o[5] = r.drho; o[6] = r.S; o[7] = 1.0 + r.rho_eq_m1;
+            o[4] = r.tau_M; o[5] = r.drho; o[6] = r.S; o[7] = 1.0 + r.rho_eq_m1; o[8] = r.tau_lb;
         }
     work_free(&w);
     return 0;
