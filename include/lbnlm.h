@@ -56,8 +56,19 @@ enum { LB_STRESS_INLM = 0, LB_STRESS_TIMESTEPPED = 1 };
  * increments below half a BF16 step survive on average) instead of to nearest;
  * LB_GRID_NO_GRAPH launches every tile-kernel step separately (by default lb_step replays runs of
  * plain tile-kernel steps from a captured CUDA graph: the same kernels with the same arguments,
- * bitwise the same result, without the per-launch host overhead). */
-enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2, LB_GRID_BF16_STOCHASTIC = 4, LB_GRID_NO_GRAPH = 8 };
+ * bitwise the same result, without the per-launch host overhead).
+ * The comparison schemes of Sec. II C (the usual alternatives to the paper's forcing; at most one,
+ * stress mode 0, periodic x and bounce-back walls, tile kernel, not in lb_run_until_steady):
+ * LB_GRID_GENERALIZED_NEWTONIAN relaxes each node with tau_LB(gdot) = 1/2 + eta_eff/(rho0 c_s^2)
+ * (Eq. taulb with the model's steady-shear viscosity eta_eff = G_inf tau_M + G_inf tau0, tau_M of
+ * Eq. nlmaxwell at the node's shear rate) and keeps only the body-force terms of Eq. (bodyforce);
+ * the stress reported is G_inf tau_M D (no normal-stress differences).
+ * LB_GRID_STRESS_DIVERGENCE feeds f^nN = div Sigma^nN (three-point differences of the same-time
+ * stress of every node, Sigma^nN = sigma + (G_inf tau0 - eta^N) D) as a force density into
+ * Eq. (rhoj) and the force terms of Eq. (bodyforce) instead of the stress line and the
+ * flow-induced density (two launches per step).  Both have delta rho = 0. */
+enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2, LB_GRID_BF16_STOCHASTIC = 4, LB_GRID_NO_GRAPH = 8,
+       LB_GRID_GENERALIZED_NEWTONIAN = 16, LB_GRID_STRESS_DIVERGENCE = 32 };
 
 typedef struct {
     int n_channels;   /* >= 1                                                              */

@@ -36,6 +36,14 @@ extern template cudaError_t launch_step_tile<double, float, 0>(const StepArgs<do
 extern template cudaError_t launch_step_tile<double, float, 1>(const StepArgs<double, float>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<float, double, 0>(const StepArgs<float, double>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<float, double, 1>(const StepArgs<float, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<double, double, 0, 1>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<double, double, 0, 2>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<float, float, 0, 1>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<float, float, 0, 2>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<__nv_bfloat16, float, 0, 1>(const StepArgs<__nv_bfloat16, float>&, int, size_t,
+                                                                         cudaStream_t);
+extern template cudaError_t launch_step_tile<__nv_bfloat16, float, 0, 2>(const StepArgs<__nv_bfloat16, float>&, int, size_t,
+                                                                         cudaStream_t);
 extern template cudaError_t launch_step_march<float, float, 0>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t launch_step_march<float, float, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
@@ -333,6 +341,8 @@ struct lb_handle {
     size_t tsize = 0, csize = 0;  // storage / arithmetic element sizes
     // device state
     void *popA = nullptr, *popB = nullptr, *drho = nullptr, *sig3 = nullptr, *sig4 = nullptr, *uprev = nullptr;
+    void* snn = nullptr;  // stress-divergence scheme: Sigma^nN of the current step [3 planes]
+    int scheme = 0;       // 0: the paper's forcing; 1: generalized Newtonian; 2: div Sigma^nN force
     void* chan = nullptr;
     WorkItem* items_d = nullptr;
     int* item_begin_d = nullptr;
@@ -428,6 +438,14 @@ std::vector<ChanParams<C>> make_chan(const lb_handle* h) {
         q.rho0_m1 = (C)(p.rho0 - 1.0);
         q.moving = h->moving ? 1 : 0;
         q.u_wall = (C)h->u_wall[c];
+        q.scheme = h->scheme;
+        if (h->scheme != 0) {
+            // the comparison schemes of Sec. II C: no stress line and no flow-induced density
+            q.k1 = C(0);
+            q.kdr = C(0);
+            q.gn_a = (C)(3.0 * p.G_inf / p.rho0);
+            q.gn_b = (C)(0.5 + 3.0 * p.G_inf * p.tau0 / p.rho0);
+        }
         if (h->gpbc) {
             // GPBC (Sec. II B): the pressure gradient replaces the body force, p_+ - p_- = g (nx+1)
             // between the ghost columns; no flow-induced density, Eq. (bodyforce) first line only
@@ -521,7 +539,7 @@ bool make_pop_map(const lb_handle* h, void* base, CUtensorMap* map) {
 lb_status plan_march(lb_handle* h) {
     h->march = false;
     if (h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
-        h->ny[0] < 16 || (h->flags & LB_GRID_TILE_ONLY))
+        h->ny[0] < 16 || (h->flags & LB_GRID_TILE_ONLY) || h->scheme != 0)
         return LB_OK;
     if (!make_pop_map(h, h->popA, &h->mapA) || !make_pop_map(h, h->popB, &h->mapB)) return LB_OK;
     h->mapA_buf = h->popA;
@@ -587,6 +605,12 @@ lb_status validate(const lb_grid* g, const lb_params* p, const lb_boundary* b) {
     if ((b->walls != LB_WALLS_BOUNCE_BACK && b->walls != LB_WALLS_COUETTE) ||
         (b->x_mode != LB_X_PERIODIC && b->x_mode != LB_X_GPBC))
         return fail(LB_EINVAL, "lb_create: walls must be LB_WALLS_BOUNCE_BACK or LB_WALLS_COUETTE and x_mode LB_X_PERIODIC or LB_X_GPBC%s");
+    const bool gn = (g->flags & LB_GRID_GENERALIZED_NEWTONIAN) != 0, dv = (g->flags & LB_GRID_STRESS_DIVERGENCE) != 0;
+    if (gn && dv) return fail(LB_EINVAL, "lb_create: choose one comparison scheme%s");
+    if ((gn || dv) && (g->stress_mode != 0 || b->walls != LB_WALLS_BOUNCE_BACK || b->x_mode != LB_X_PERIODIC))
+        return fail(LB_EINVAL, "lb_create: the comparison schemes run with stress mode 0, periodic x and bounce-back walls%s");
+    if ((gn || dv) && g->precision != LB_PREC_F64 && g->precision != LB_PREC_F32 && g->precision != LB_PREC_BF16)
+        return fail(LB_EINVAL, "lb_create: the comparison schemes run in FP64, FP32 or BF16%s");
     for (int c = 0; c < g->n_channels; ++c) {
         if (g->ny[c] < 3) return fail(LB_EINVAL, "lb_create: ny must be >= 3%s");
         if ((long long)g->ny[c] * g->nx > (1ll << 40)) return fail(LB_EINVAL, "lb_create: channel too large%s");
@@ -612,7 +636,7 @@ void free_dev(T*& p) {
 void release(lb_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    free_dev(h->popA); free_dev(h->popB); free_dev(h->drho); free_dev(h->sig3); free_dev(h->sig4);
+    free_dev(h->popA); free_dev(h->popB); free_dev(h->drho); free_dev(h->sig3); free_dev(h->sig4); free_dev(h->snn);
     free_dev(h->uprev); free_dev(h->chan); free_dev(h->items_d); free_dev(h->item_begin_d);
     free_dev(h->partials); free_dev(h->mon_d); free_dev(h->status_d); free_dev(h->base_d); free_dev(h->P_d);
     free_dev(h->node_off_d); free_dev(h->ny_d); free_dev(h->gx_d); free_dev(h->fields); free_dev(h->fconv);
@@ -666,6 +690,7 @@ StepArgs<T, C> base_args(lb_handle* h) {
     a.sig3 = (C*)h->sig3;
     a.sig4 = (C*)h->sig4;
     a.uprev = (C*)h->uprev;
+    a.snn = (C*)h->snn;
     a.partials = h->partials;
     a.items = h->items_d;
     a.chan = (const ChanParams<C>*)h->chan;
@@ -707,9 +732,30 @@ cudaError_t gpbc_columns(lb_handle* h) {
                                      h->gny, h->gpbc_max_ny, h->gpart, h->gcount, h->stream);
 }
 
+// The comparison schemes are instantiated for the three main precisions (T and C of one type, or
+// BF16 storage with FP32 arithmetic); lb_create refuses them with the mixed diagnostic ones.
+template <typename T, typename C>
+constexpr bool kSchemeTypes = std::is_same<T, C>::value || std::is_same<T, __nv_bfloat16>::value;
+
 template <typename T, typename C>
 cudaError_t launch(lb_handle* h, const StepArgs<T, C>& a) {
     const int n = (int)h->items.size();
+    if constexpr (kSchemeTypes<T, C>) {
+        if (h->scheme == 1) return launch_step_tile<T, C, 0, 1>(a, n, h->smem, h->stream);
+        if (h->scheme == 2) {
+            // stress divergence: Sigma^nN of every node of this step first, then the step (or the
+            // fields pass) that differentiates it
+            StepArgs<T, C> s = a;
+            s.flags = F_SNN;
+            cudaError_t e = launch_step_tile<T, C, 0, 2>(s, n, h->smem, h->stream);
+            if (e != cudaSuccess) return e;
+            StepArgs<T, C> b = a;
+            b.flags |= F_DIV;
+            return launch_step_tile<T, C, 0, 2>(b, n, h->smem, h->stream);
+        }
+    } else {
+        if (h->scheme != 0) return cudaErrorNotSupported;
+    }
     if (h->smode == 0) return launch_step_tile<T, C, 0>(a, n, h->smem, h->stream);
     return launch_step_tile<T, C, 1>(a, n, h->smem, h->stream);
 }
@@ -1149,6 +1195,8 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
     if (h->smode != 0) return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements stress mode 0%s");
     if (h->gpbc || h->moving)
         return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements periodic x and bounce-back walls only%s");
+    if (h->scheme != 0)
+        return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements the paper's scheme only (step comparison schemes with lb_step)%s");
     if (h->prec == LB_PREC_F64S_F32M || h->prec == LB_PREC_F32S_F64M)
         return fail(LB_EINVAL, "lb_run_until_steady: diagnostic precision mixes are not supported%s");
     // Segments of growing length (64, 256, 1024, ... check intervals): after each one the
@@ -1305,6 +1353,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     h->prec = grid->precision;
     h->smode = grid->stress_mode;
     h->flags = grid->flags;
+    h->scheme = (grid->flags & LB_GRID_GENERALIZED_NEWTONIAN) ? 1 : ((grid->flags & LB_GRID_STRESS_DIVERGENCE) ? 2 : 0);
     h->tsize = with_types(h->prec, [](auto tt, auto tc) { LB_TYPES(tt, tc); (void)sizeof(C); return sizeof(T); });
     h->csize = with_types(h->prec, [](auto tt, auto tc) { LB_TYPES(tt, tc); (void)sizeof(T); return sizeof(C); });
     h->ny.assign(grid->ny, grid->ny + h->n_ch);
@@ -1342,6 +1391,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     LB_ALLOC(h->popB, 9 * h->planes * h->tsize);
     LB_ALLOC(h->drho, h->planes * h->csize);
     if (h->smode == 1) LB_ALLOC(h->sig3, 3 * h->planes * h->csize);
+    if (h->scheme == 2) LB_ALLOC(h->snn, 3 * h->planes * h->csize);
     if (h->flags & LB_GRID_STORE_SIGMA) LB_ALLOC(h->sig4, 4 * h->planes * h->csize);
     LB_ALLOC(h->uprev, 2 * h->planes * h->csize);
     LB_ALLOC(h->chan, h->n_ch * (h->csize == 8 ? sizeof(ChanParams<double>) : sizeof(ChanParams<float>)));

@@ -106,6 +106,7 @@ struct ChanParams {
     int gpbc;     // 1: generalized periodic boundaries along x (pressure-driven, Sec. II B)
     int row_off;  // first row of the channel in the stacked boundary-column arrays (GPBC)
     int moving;   // 1: the last row lies on a wall moving with (u_wall, 0) (Zou-He, Sec. IV C)
+    int scheme;   // 0: the paper's forcing; 1: generalized Newtonian; 2: div Sigma^nN as a force
     C omega;    // 1/tau_LB (BGK)
     C k1;       // -1/(2 c_s^4 tau_LB) = -9/(2 tau_LB): traceless-stress line of Eq. (bodyforce)
     C k2;       // 1 - 1/(2 tau_LB)
@@ -119,6 +120,8 @@ struct ChanParams {
     C rho_in;   // GPBC: c_s^-2 p_+ - 1 at the inlet ghost column x = -1 (densities near 1 are kept
     C rho_out;  //       as offsets from 1, like the populations); c_s^-2 p_- - 1 at x = nx
     C u_wall;   // tangential velocity of the moving wall (moving == 1)
+    C gn_a;     // scheme 1: tau_LB(gdot) = gn_b + gn_a tau_M, gn_a = G_inf / (rho0 c_s^2)
+    C gn_b;     //           gn_b = 1/2 + eta_inf / (rho0 c_s^2)  (Eq. taulb with eta_eff)
 };
 
 struct WorkItem {
@@ -137,6 +140,8 @@ enum : int {
     F_RESID = 8,        // accumulate the residual against u_prev (block partials)
     F_SR = 16,          // BF16 storage: stochastic rounding of the populations
     F_MON = 32,         // accumulate flux and max |u| only (block partials; no u_prev read)
+    F_SNN = 64,         // scheme 2, first pass: write Sigma^nN (xx, xy, yy) only (no state writes)
+    F_DIV = 128,        // scheme 2, second pass: add div Sigma^nN of the written planes as a force
 };
 
 template <typename T, typename C>
@@ -151,6 +156,7 @@ struct StepArgs {
     C* __restrict__ fsig;          //   sigma [node][4]
     C* __restrict__ frho;          //   rho [node]
     double* __restrict__ partials; // residual partials [item][4]
+    C* __restrict__ snn;           // scheme 2: Sigma^nN (xx, xy, yy) of this step [3 planes]
     const WorkItem* __restrict__ items;
     const ChanParams<C>* __restrict__ chan;
     int* __restrict__ status;      // per channel: 0 stable, 1 unstable
@@ -177,6 +183,14 @@ template <> struct Arith<double> {
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
 };
+#ifdef LBK_FP32_IEEE
+// Compile-time alternative: correctly rounded FP32 division and square root (IEEE round to
+// nearest even), for measuring what the approximations cost in parity and in throughput.
+template <> struct Arith<float> {
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqrt(float x) { return __fsqrt_rn(x); }
+};
+#else
 template <> struct Arith<float> {
     static __device__ __forceinline__ float rcp(float x) {
         float r;
@@ -190,6 +204,7 @@ template <> struct Arith<float> {
         return x >= 1.17549435e-38f ? x * r : 0.f;
     }
 };
+#endif
 
 // Moments of Eq. (rhoj) from the post-streaming deviations: dR = sum_i n_i - 1, J0 = sum c_i n_i.
 template <typename C>
@@ -305,6 +320,31 @@ __device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C k
     return r;
 }
 
+// Scheme 1 (generalized Newtonian, the first alternative of Sec. II C): a locally Newtonian fluid
+// whose viscosity is the model's effective viscosity in steady shear, eta_eff = G tau_M + eta_inf,
+// through Eq. (taulb): tau_LB = 1/2 + eta_eff/(rho0 c_s^2).  No stress line, no flow-induced
+// density; the reported stress is G tau_M D.  Returns the node's 1/tau_LB in *omega.
+template <typename C>
+__device__ __forceinline__ NodeState<C> constitutive_gn(const ChanParams<C>& P, C ka, C kb, C kc, C ke, C dR, C jx,
+                                                        C jy, C* omega) {
+    NodeState<C> r;
+    const C Dxx = C(2) * ka, Dxy = kb + kc, Dyy = C(2) * ke;
+    const C II = C(0.5) * (Dxx * Dxx + C(2) * Dxy * Dxy + Dyy * Dyy);
+    const C tau_M = Arith<C>::div(P.tau, C(1) + P.tau * Arith<C>::sqrt(II) * P.inv_gc);
+    const C gt = P.G * tau_M;
+    r.sxx = gt * Dxx;
+    r.sxy = gt * Dxy;
+    r.syy = gt * Dyy;
+    r.Bxx = r.Bxy = C(0);
+    r.drho = r.S = C(0);
+    r.dReq = dR;
+    const C inv = Arith<C>::div(C(1), C(1) + dR);
+    r.ux = jx * inv;
+    r.uy = jy * inv;
+    *omega = Arith<C>::div(C(1), P.gn_b + P.gn_a * tau_M);
+    return r;
+}
+
 // Collision increments D_i = Delta_i + F_i = F_i + (n^eq_i - n_i)/tau_LB, with n^eq of Eq. (neq)
 // as an offset from w_i and F_i of Eq. (bodyforce).  Opposite directions share the parts that are
 // even in c_i (E) and differ in the sign of the odd part (O):
@@ -317,15 +357,23 @@ __device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C k
 // increments are closed from those conditions instead of being evaluated: direction 3 from the
 // x momentum f_x, direction 4 from the y momentum 0, and the rest direction from the mass S.
 // In exact arithmetic the closed values equal the evaluated ones.
-template <typename C>
-__device__ __forceinline__ void collide_node(const ChanParams<C>& P, const NodeState<C>& s, const C (&d)[9], C (&D)[9]) {
-    const C ux = s.ux, uy = s.uy, om = P.omega, k2 = P.k2, gx = P.gx;
+// GEN = true (the comparison schemes): the node's own om = 1/tau_LB and k2 = 1 - om/2, and a force
+// density (gx, fy) with a y component; GEN = false is the paper's scheme with the channel's
+// constants and f = (g_x, 0).
+template <typename C, bool GEN>
+__device__ __forceinline__ void collide_impl(const ChanParams<C>& P, const NodeState<C>& s, const C (&d)[9], C (&D)[9],
+                                             C om, C k2, C gx, C fy) {
+    const C ux = s.ux, uy = s.uy;
     const C rq = C(1) + s.dReq;
     const C orq = om * rq;
     const C usq = ux * ux + uy * uy;
-    const C Yxx = -s.S * ux * ux + C(2) * ux * gx;
-    const C Yyy = -s.S * uy * uy;
-    const C Yxy = -s.S * ux * uy + uy * gx;
+    C Yxx = -s.S * ux * ux + C(2) * ux * gx;
+    C Yyy = -s.S * uy * uy;
+    C Yxy = -s.S * ux * uy + uy * gx;
+    if constexpr (GEN) {
+        Yyy += C(2) * uy * fy;
+        Yxy += ux * fy;
+    }
     const C trY3 = (Yxx + Yyy) * (C(1) / C(3));
     const C base = om * (s.dReq - C(1.5) * rq * usq) + k2 * s.S;
     const C w1 = wgt<C>(1), w5 = wgt<C>(5);
@@ -340,14 +388,16 @@ __device__ __forceinline__ void collide_node(const ChanParams<C>& P, const NodeS
     {
         const C cu = uy;
         const C E = w1 * (base + C(4.5) * (orq * cu * cu + k2 * (Yyy - trY3)) - P.k1 * s.Bxx);
-        const C O = w1 * C(3) * (orq * cu);
+        C O = w1 * C(3) * (orq * cu);
+        if constexpr (GEN) O = w1 * C(3) * (orq * cu + k2 * fy);
         D[2] = E + O - om * d[2];
     }
     // (5, 7): c = +-(1, 1)
     {
         const C cu = ux + uy;
         const C E = w5 * (base + C(4.5) * (orq * cu * cu + k2 * (Yxx + Yyy + C(2) * Yxy - trY3)) + C(2) * P.k1 * s.Bxy);
-        const C O = w5 * C(3) * (orq * cu + k2 * gx);
+        C O = w5 * C(3) * (orq * cu + k2 * gx);
+        if constexpr (GEN) O = w5 * C(3) * (orq * cu + k2 * (gx + fy));
         D[5] = E + O - om * d[5];
         D[7] = E - O - om * d[7];
     }
@@ -355,15 +405,22 @@ __device__ __forceinline__ void collide_node(const ChanParams<C>& P, const NodeS
     {
         const C cu = ux - uy;
         const C E = w5 * (base + C(4.5) * (orq * cu * cu + k2 * (Yxx + Yyy - C(2) * Yxy - trY3)) - C(2) * P.k1 * s.Bxy);
-        const C O = w5 * C(3) * (orq * cu + k2 * gx);
+        C O = w5 * C(3) * (orq * cu + k2 * gx);
+        if constexpr (GEN) O = w5 * C(3) * (orq * cu + k2 * (gx - fy));
         D[8] = E + O - om * d[8];
         D[6] = E - O - om * d[6];
     }
-    // closures: sum c_x D = f_x, sum c_y D = 0, sum D = S
+    // closures: sum c_x D = f_x, sum c_y D = f_y (0 in the paper's scheme), sum D = S
     const C d57 = D[5] - D[7];
     D[3] = D[1] + d57 + (D[8] - D[6]) - gx;
-    D[4] = D[2] + d57 + (D[6] - D[8]);
+    if constexpr (GEN) D[4] = D[2] + d57 + (D[6] - D[8]) - fy;
+    else D[4] = D[2] + d57 + (D[6] - D[8]);
     D[0] = s.S - (((D[1] + D[2]) + (D[3] + D[4])) + ((D[5] + D[6]) + (D[7] + D[8])));
+}
+
+template <typename C>
+__device__ __forceinline__ void collide_node(const ChanParams<C>& P, const NodeState<C>& s, const C (&d)[9], C (&D)[9]) {
+    collide_impl<C, false>(P, s, d, D, P.omega, P.k2, P.gx, C(0));
 }
 
 // |u| <= guard for the reported velocity j/rho_h without a division or square root (false for NaN).

@@ -9,6 +9,9 @@
 //   phase 3  kappa by three-point differences from shared memory (central; one-sided second
 //            order on the first/last fluid row), the nlM stress, Sigma^nN, delta rho, n^eq, F_i
 //            and the BGK collision; store n*, delta rho, optional stress / velocity / residual.
+// The comparison schemes of Sec. II C run here too: the generalized-Newtonian tau_LB(gdot)
+// (scheme 1) and the divergence of Sigma^nN as a force density (scheme 2, two launches per step:
+// F_SNN writes Sigma^nN of every node, then the step with F_DIV differentiates it).
 // A full-width tile (nxt == nx) wraps x inside the tile and needs no x halo.
 #pragma once
 
@@ -64,8 +67,9 @@ __device__ __forceinline__ C warp_max(C v) {
     return v;
 }
 
-// Block size: NT threads; tile nxt*nyt <= NT.
-template <typename T, typename C, int SMODE, int NT>
+// Block size: NT threads; tile nxt*nyt <= NT.  SCHEME: 0 the paper's forcing; 1, 2 the comparison
+// schemes (compile-time, so that the paper's instantiation carries none of their code).
+template <typename T, typename C, int SMODE, int NT, int SCHEME = 0>
 __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* su = reinterpret_cast<C*>(smem_raw);  // [EY*EX][2] gradient velocity
@@ -166,7 +170,45 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
             so_xy = s3[P.P + pn];
             so_yy = s3[2 * P.P + pn];
         }
-        const NodeState<C> s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dR, jx, jy, drho_prev, so_xx, so_xy, so_yy);
+        // the comparison schemes of Sec. II C use their own relaxation rate / force (collide_impl)
+        C om = P.omega, k2 = P.k2, fx = P.gx, fy = C(0);
+        NodeState<C> s;
+        if constexpr (SCHEME == 1) {
+            s = constitutive_gn<C>(P, ka, kb, kc, ke, dR, jx, jy, &om);
+            k2 = C(1) - C(0.5) * om;
+        } else {
+            s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dR, jx, jy, drho_prev, so_xx, so_xy, so_yy);
+        }
+        if (SCHEME == 2 && (a.flags & F_SNN)) {
+            // scheme 2, first pass: Sigma^nN = sigma + (eta_inf - eta^N) D of every node of this step
+            C* q = a.snn + 3 * P.base;
+            q[pn] = s.sxx + P.cD * (C(2) * ka);
+            q[P.P + pn] = s.sxy + P.cD * (kb + kc);
+            q[2 * P.P + pn] = s.syy + P.cD * (C(2) * ke);
+        } else {
+        if (SCHEME == 2 && (a.flags & F_DIV)) {
+            // scheme 2, second pass: f^nN = div Sigma^nN by three-point differences (central along
+            // the periodic x axis and inside the channel, one-sided on the first and last row),
+            // added to the force density in j (Eq. rhoj) and in the force terms of Eq. (bodyforce)
+            const C* q = a.snn + 3 * P.base;
+            const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+            auto at = [&](int comp, int yy, int xx) -> C { return q[comp * P.P + (long long)yy * nx + xx]; };
+            auto ddy = [&](int comp) -> C {
+                if (y == 0) return C(0.5) * (C(-3) * at(comp, 0, x) + C(4) * at(comp, 1, x) - at(comp, 2, x));
+                if (y == ny - 1)
+                    return C(0.5) * (C(3) * at(comp, ny - 1, x) - C(4) * at(comp, ny - 2, x) + at(comp, ny - 3, x));
+                return C(0.5) * (at(comp, y + 1, x) - at(comp, y - 1, x));
+            };
+            const C fnx = C(0.5) * (at(0, y, xp) - at(0, y, xm)) + ddy(1);
+            const C fny = C(0.5) * (at(1, y, xp) - at(1, y, xm)) + ddy(2);
+            fx += fnx;
+            fy += fny;
+            jx += C(0.5) * fnx;
+            jy += C(0.5) * fny;
+            const C inv = Arith<C>::div(C(1), C(1) + s.dReq);
+            s.ux = jx * inv;
+            s.uy = jy * inv;
+        }
 
         // reported fields: hydrodynamic density rho_eq - delta rho (Eq. rhoj), u = j / rho
         const C rho_h = C(1) + s.dReq - s.drho;
@@ -189,7 +231,8 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
             a.frho[node] = rho_h;
         } else {
             C D[9];
-            collide_node<C>(P, s, d, D);
+            if constexpr (SCHEME != 0) collide_impl<C, true>(P, s, d, D, om, k2, fx, fy);
+            else collide_node<C>(P, s, d, D);
             T* po = a.pout + 9 * P.base + pn;
             store_node<T, C>(po, P.P, d, D, (a.flags & F_SR) != 0, a.sr_key ^ (uint32_t)(it.ch * 0x9E3779B9u), (uint32_t)pn);
             dr[pn] = s.drho;
@@ -222,6 +265,7 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
                 up[P.P + pn] = ury;
             }
         }
+        }  // not the Sigma^nN pass
     }
     if (a.flags & (F_RESID | F_MON)) {
         // block reduction of (sum du^2, sum u^2, sum u_x, max |u|) in double
@@ -307,10 +351,10 @@ cudaError_t launch_gpbc_columns(const T* pin, const ChanParams<C>* chan, C* gcol
 }
 
 // Host-side launcher, explicitly instantiated per storage type in lb_kernels_*.cu.
-template <typename T, typename C, int SMODE>
+template <typename T, typename C, int SMODE, int SCHEME = 0>
 cudaError_t launch_step_tile(const StepArgs<T, C>& a, int n_items, size_t smem, cudaStream_t s) {
     constexpr int NT = 256;
-    auto k = k_step_tile<T, C, SMODE, NT>;
+    auto k = k_step_tile<T, C, SMODE, NT, SCHEME>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

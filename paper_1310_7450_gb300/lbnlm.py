@@ -22,6 +22,9 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = ra
 LB_PREC_F64, LB_PREC_F32, LB_PREC_BF16 = 0, 1, 2
 LB_STRESS_INLM, LB_STRESS_TIMESTEPPED = 0, 1
 LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY, LB_GRID_BF16_STOCHASTIC, LB_GRID_NO_GRAPH = 1, 2, 4, 8
+LB_GRID_GENERALIZED_NEWTONIAN, LB_GRID_STRESS_DIVERGENCE = 16, 32
+SCHEME_FLAGS = {"paper": 0, "generalized_newtonian": LB_GRID_GENERALIZED_NEWTONIAN,
+                "stress_divergence": LB_GRID_STRESS_DIVERGENCE}
 LB_X_PERIODIC, LB_X_GPBC = 1, 2
 X_MODES = {"periodic": LB_X_PERIODIC, "gpbc": LB_X_GPBC}
 LB_WALLS_BOUNCE_BACK, LB_WALLS_COUETTE = 1, 2
@@ -355,12 +358,13 @@ class Channels:
     """Owns one handle; returns fields as NumPy arrays shaped per channel."""
 
     def __init__(self, nx, ny, params, precision="f64", stress_mode=0, flags=0, stream=None, x_mode="periodic",
-                 walls="bounce_back"):
+                 walls="bounce_back", scheme="paper"):
         self.nx = int(nx)
         self.ny = [int(ny)] if np.isscalar(ny) else [int(v) for v in ny]
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         xm = X_MODES[x_mode] if isinstance(x_mode, str) else int(x_mode)
         wl = WALLS[walls] if isinstance(walls, str) else int(walls)
+        flags = int(flags) | SCHEME_FLAGS[scheme]
         self.h = lb_create(self.nx, self.ny, params, prec, stress_mode, flags, stream, xm, wl)
         self.nodes = lb_num_nodes(self.h)
 

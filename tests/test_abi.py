@@ -115,3 +115,18 @@ def test_wait_limit_validation_before_device_work(lib):
 def test_monitor_mode_validation_before_device_work(lib):
     from paper_1310_7450_gb300 import lbnlm
     assert lib.lb_set_monitor_mode(None, lbnlm.LB_MONITOR_FLUX_MAX) == lbnlm.LB_EINVAL
+
+
+@pytest.mark.parametrize("flags,stress_mode,x_mode,walls", [
+    (16 | 32, 0, 1, 1),   # both comparison schemes
+    (16, 1, 1, 1),        # generalized Newtonian with the time-stepped stress
+    (32, 0, 2, 1),        # stress divergence with pressure-driven ends
+    (16, 0, 1, 2),        # generalized Newtonian with a moving wall
+])
+def test_comparison_scheme_combinations_rejected_before_device_work(lib, flags, stress_mode, x_mode, walls):
+    from paper_1310_7450_gb300 import lbnlm
+    p = dict(tau_lb=0.9, g_x=1e-6, G_inf=1e-3, tau0=1.0, theta=10.0, gamma_c=0.1, rho0=1.0)
+    with pytest.raises(lbnlm.LBError) as e:
+        lbnlm.lb_create(4, 16, p, 0, stress_mode, flags, None, x_mode, walls)
+    assert e.value.status == lbnlm.LB_EINVAL
+    assert "scheme" in lbnlm.lb_last_error()

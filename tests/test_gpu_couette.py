@@ -71,9 +71,8 @@ def test_couette_startup_and_cessation(stream, prec, tol):
     uo2, so2, _ = oracle.fields(cou(p, 0.0), st)
     print(f"Couette {prec}: start-up u {rel(u1, uo1):.2e} sigma {rel(s1, so1):.2e}; "
           f"cessation u {rel(u2, uo2):.2e} sigma {rel(s2, so2):.2e}")
-    stol = tol if prec == "f64" else 5e-5
-    assert rel(u1, uo1) < tol and rel(s1, so1) < stol
-    assert rel(u2, uo2) < tol and rel(s2, so2) < stol
+    assert rel(u1, uo1) < tol and rel(s1, so1) < tol
+    assert rel(u2, uo2) < tol and rel(s2, so2) < tol
 
 
 def test_couette_with_pressure_driven_ends(stream):

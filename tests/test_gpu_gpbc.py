@@ -74,9 +74,11 @@ def test_gpbc_linear_start_matches_input_generator(stream):
 def test_gpbc_yield_stress_channel_from_linear_start(stream, prec, tol):
     """4 x 64 yield-stress channel (theta = 100, gamma_c = 0.1, wp H = 1/2) started from the
     linear density, 20000 steps.  FP32 bound 1e-4 rather than the body-force channel's 1e-5: the
-    drive is now a density difference of 3 g = 6e-7 between neighbouring columns, carried by
-    populations whose velocity part is ~1e-2, so each node's FP32 density (a sum of nine
-    deviations) resolves it only to ~1e-3 (measured: u 5.9e-5, sigma 6.5e-5)."""
+    drive is now a density difference of 3 g = 6.2e-7 between neighbouring columns, while every
+    node's density is a sum of nine FP32 deviations whose velocity parts reach w_i 3 c.u ~ 1.7e-2
+    (unit in the last place 1.9e-9), so each node resolves its share of the drive only to ~1e-2,
+    and the flow averages these errors over the nodes and the ~1e4 steps of the viscous time
+    (measured: u 5.9e-5, sigma 6.5e-5, 2.7x the stress floor of the FP32 velocity)."""
     cfg = inputs.oracle_channel_yield()
     nx, ny, p = cfg["nx"], cfg["ny"], cfg["params"]
     with lbnlm.Channels(nx, ny, p, prec, stream=stream, x_mode="gpbc") as sim:
@@ -86,7 +88,8 @@ def test_gpbc_yield_stress_channel_from_linear_start(stream, prec, tol):
     st = oracle.init_state(inputs.linear_density(nx, ny, rin, rout))
     oracle.run(gp(p), st, 20000)
     u_o, s_o, _ = oracle.fields(gp(p), st)
-    print(f"GPBC {prec}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e}")
+    floor = p["G_inf"] * p["theta"] * p["tau0"] * float(np.spacing(np.float32(np.abs(u_o).max()))) / np.abs(s_o).max()
+    print(f"GPBC {prec}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e}, sigma floor {floor:.2e}")
     assert rel(u_g, u_o) < tol
     assert rel(s_g, s_o) < tol
 
@@ -180,13 +183,16 @@ def test_row_march_boundary_variant_matches_tile_kernel_and_oracle(stream, prec,
             res[flags] = (u, s, n)
     u_m, s_m, n_m = res[0]
     u_t, s_t, n_t = res[lbnlm.LB_GRID_TILE_ONLY]
-    w = oracle.WEIGHTS[:, None, None]
-    print(f"{prec} nx={nx} {x_mode}/{walls}: march vs tile u {rel(u_m, u_t):.2e}, populations {rel(n_m - w, n_t - w):.2e}")
+    # the boundary variants apply the same rules with the same arithmetic as the tile kernel
+    assert np.array_equal(n_m, n_t) and np.array_equal(u_m, u_t) and np.array_equal(s_m, s_t)
+    po = dict(p, x_mode=x_mode, top_wall="moving" if walls == "couette" else "bounce_back", u_wall=0.01)
+    oracle.run(po, st, 60)
+    u_o, _, _ = oracle.fields(po, st)
+    print(f"{prec} nx={nx} {x_mode}/{walls}: row march vs oracle u {rel(u_m, u_o):.2e}")
     if prec == "f32":
-        assert rel(u_m, u_t) < 1e-5 and rel(n_m - w, n_t - w) < 1e-5
-        po = dict(p, x_mode=x_mode, top_wall="moving" if walls == "couette" else "bounce_back", u_wall=0.01)
-        oracle.run(po, st, 60)
-        u_o, _, _ = oracle.fields(po, st)
-        assert rel(u_m, u_o) < 1e-4
+        assert rel(u_m, u_o) < 1e-5   # (60 steps: far from the drift of the 20000-step run above)
     else:
-        assert rel(u_m, u_t) < 1e-2
+        # units of BF16 roundoff 2^-9: four as on the periodic channel; with pressure-driven ends the
+        # drive is a density step per column that BF16 deviations resolve even more coarsely than
+        # FP32 ones (test above), eight there (measured 9.5e-3 at nx = 128, 6.6e-3 at nx = 384)
+        assert rel(u_m, u_o) < (8 if x_mode == "gpbc" else 4) * 2.0 ** -9

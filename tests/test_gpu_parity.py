@@ -40,6 +40,16 @@ def nlm(theta=10.0, g=1e-5, G=1e-3):
     return inputs.matched_params(0.9, theta, 0.1, G, g)
 
 
+def fp32_stress_floor(p, u_o, s_o):
+    """What one FP32 rounding of the velocity costs the stress, relative to max |sigma|: an error
+    of one unit in the last place of max |u| enters kappa as a row or column difference, and the
+    stress sigma = G tau_M kappa + ... carries it with G tau_M <= G tau.  With G tau ~ 0.1 (the
+    yield-stress channels) this floor lies above 1e-5, so no FP32 velocity can meet 1e-5 on the
+    stress there."""
+    ulp_u = float(np.spacing(np.float32(np.abs(u_o).max())))
+    return p["G_inf"] * p["theta"] * p["tau0"] * ulp_u / np.abs(s_o).max()
+
+
 GRIDS = [(4, 200), (40, 13), (70, 29), (1, 10), (2, 3), (128, 5), (129, 7), (33, 17)]
 
 
@@ -56,7 +66,7 @@ def test_fp64_random_state_matches_oracle(stream, nx, ny):
     u_o, s_o, r_o = oracle.fields(p, st)
     # populations as full values (the oracle stores n, not n - w: its own rounding is ~1e-16 of n)
     assert rel(n_g, st.nstar) < 1e-14
-    assert rel(d_g, st.drho) < 1e-10
+    assert rel(d_g, st.drho) < 1e-12
     assert rel(u_g, u_o) < 1e-12
     assert rel(s_g, s_o) < 1e-11
     assert rel(r_g - 1, r_o - 1) < 1e-11
@@ -94,9 +104,10 @@ def test_fp64_newtonian_channel(stream):
 @pytest.mark.parametrize("mode", [0, 1])
 def test_fp32_yield_stress_channel(stream, mode):
     """FP32 storage and arithmetic, 4 x 64 channel at theta = 100 (tau = 1e4), 20000 steps from rest.
-    u meets 1e-5.  sigma is bounded by the FP32 storage itself: in the plug sigma_xy = G tau kappa
-    amplifies the rounding of the stored populations (FP32 storage with FP64 arithmetic measured
-    1.7e-5, the FP32 path 3.2e-5 relative to max |sigma|), so the stress bound here is 5e-5."""
+    u meets 1e-5.  The stress is bounded by the FP32 velocity itself: with G tau = 0.13 one unit in
+    the last place of max |u| is 2.4e-5 of max |sigma| (fp32_stress_floor), so the bound is 1.5x that
+    floor (measured: 0.83x in both stress modes; FP32 storage with FP64 arithmetic 0.71x; IEEE
+    division and square root instead of the single-instruction approximations 0.91x)."""
     cfg = inputs.oracle_channel_yield()
     p = dict(cfg["params"], stress_mode=mode)
     nx, ny, steps = cfg["nx"], cfg["ny"], cfg["steps"]
@@ -106,8 +117,11 @@ def test_fp32_yield_stress_channel(stream, mode):
     st = oracle.init_state(np.ones((ny, nx)))
     oracle.run(p, st, steps)
     u_o, s_o, _ = oracle.fields(p, st)
+    floor = fp32_stress_floor(p, u_o, s_o)
+    print(f"theta 100 FP32 mode {mode}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e} = "
+          f"{rel(s_g, s_o) / floor:.2f} x floor {floor:.2e}")
     assert rel(u_g, u_o) < 1e-5
-    assert rel(s_g, s_o) < 5e-5
+    assert rel(s_g, s_o) < max(1e-5, 1.5 * floor)
 
 
 @pytest.mark.parametrize("theta", [0.0, 10.0])
@@ -138,8 +152,10 @@ def test_fp32_random_state(stream, nx, ny):
         (u_g, s_g, _), = sim.fields()
     oracle.run(p, st, 30)
     u_o, s_o, _ = oracle.fields(p, st)
+    print(f"FP32 random state {nx}x{ny}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e}, "
+          f"floor {fp32_stress_floor(p, u_o, s_o):.2e}")
     assert rel(u_g, u_o) < 1e-5
-    assert rel(s_g, s_o) < 1e-4  # sigma of random states is dominated by FD of FP32 noise
+    assert rel(s_g, s_o) < 1e-5
 
 
 def test_seeded_initial_density_matches_input_generator(stream):
@@ -456,14 +472,19 @@ def test_row_march_kernel_matches_tile_kernel_and_oracle(stream, prec, nx, ny):
             res[flags] = (u, s, n)
     u_m, s_m, n_m = res[0]
     u_t, s_t, n_t = res[lbnlm.LB_GRID_TILE_ONLY]
-    w = oracle.WEIGHTS[:, None, None]
+    # the two kernels do the same per-node arithmetic in the same order
+    assert np.array_equal(n_m, n_t) and np.array_equal(u_m, u_t) and np.array_equal(s_m, s_t)
+    oracle.run(p, st, 40)
+    u_o, s_o, _ = oracle.fields(p, st)
+    print(f"row march {prec} {nx}x{ny}: u {rel(u_m, u_o):.2e}, sigma {rel(s_m, s_o):.2e}")
     if prec == "f32":
-        assert rel(u_m, u_t) < 1e-6 and rel(n_m - w, n_t - w) < 1e-5
-        oracle.run(p, st, 40)
-        u_o, s_o, _ = oracle.fields(p, st)
-        assert rel(u_m, u_o) < 1e-5
+        assert rel(u_m, u_o) < 1e-5 and rel(s_m, s_o) < 1e-5
     else:
-        assert rel(u_m, u_t) < 1e-2
+        # BF16 keeps 8 significant bits of each stored deviation (unit roundoff 2^-9 = 1.95e-3);
+        # after 40 steps the velocity carries about two units of it and the stress, a difference
+        # quotient of the velocity, about seven (measured 4.3e-3 / 1.4e-2 at 256 x 64 and 128 x 37)
+        ubf = 2.0 ** -9
+        assert rel(u_m, u_o) < 4 * ubf and rel(s_m, s_o) < 12 * ubf
 
 
 def test_row_march_residual_matches_numpy(stream):

@@ -7,10 +7,11 @@ rounding draws per node and breaks it, so that run is compared through its x-mea
 printed per precision.  Bounds: FP32 storage within 2e-3 of the analytic steady profile; BF16 with
 stochastic rounding within 4e-3 (measured 2.8e-3 of the x-mean: the 2e-3 target of reduced storage
 is not reached by BF16 here; round to nearest drifts to 5.1e-3 and its stress is O(1) wrong in the
-plug); FP32 u within 5e-5 of the oracle -- the FP32 velocity carries
-~4e-9 absolute (ulp of 0.05), and in the plug the stress G tau kappa_xy is built from row
-differences of that size, so at this width the stress, and through it u, drift further from the
-FP64 oracle than on the narrow channels (measured: u 1.5e-5, sigma 2.6e-2 of max |sigma|)."""
+plug); FP32 u within 5e-5 of the oracle and sigma within 4x its FP32 velocity floor -- the FP32
+velocity carries ~4e-9 absolute (ulp of 0.05), and in the plug the stress G tau kappa_xy is built
+from row differences of that size, so at this width the stress, and through it u, drift further
+from the FP64 oracle than on the narrow channels (measured: u 1.5e-5, sigma 2.6e-2 of max |sigma|,
+2.2x the floor)."""
 import numpy as np
 import pytest
 
@@ -57,6 +58,12 @@ def test_reduced_precision_8192x2048():
         print(f"{name}: u vs oracle {res[name][0]:.2e}, sigma vs oracle {res[name][1]:.2e}, "
               f"u vs analytic {res[name][2]:.2e}")
     print(f"f64 oracle: u vs analytic {rel(u_o[:, 0, 0], ua):.2e}")
+    # the stress floor of the FP32 velocity: one unit in the last place of max |u| carried into
+    # sigma by G tau, relative to max |sigma| (1.2e-2 here); after 1e5 steps the row-to-row
+    # velocity errors in the plug reach about two such units (sigma 2.6e-2 = 2.2x the floor)
+    floor = p["G_inf"] * p["theta"] * p["tau0"] * float(np.spacing(np.float32(np.abs(u_o).max()))) / np.abs(s_o).max()
+    print(f"f32 sigma: {res['f32'][1] / floor:.1f} x floor {floor:.2e}")
+    assert res["f32"][1] < 4 * floor
     assert res["f32"][0] < 5e-5
     assert res["f32"][2] < 2e-3
     assert res["bf16_sr"][2] < 4e-3

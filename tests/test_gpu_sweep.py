@@ -192,8 +192,9 @@ def test_sweep_graph_replayed_across_calls(stream):
 def test_full_size_sweep_sampled_channels_match_oracle(stream):
     """The 512-channel sweep draw (seed 3) in the benchmark's launch configuration (width classes,
     tuned kernels, one graph), 2000 steps from rest: the narrowest, the widest and two middle
-    channels against the oracle (FP32: u within 1e-5; sigma within 2e-4 -- theta reaches 1e3 in
-    this draw, and the FP32 storage of the stress already sets a 1.7e-5 floor at theta = 100)."""
+    channels against the oracle (FP32: u within 1e-5; sigma within 1e-5 or 1.5x the channel's FP32
+    velocity floor, whichever is larger: one unit in the last place of max |u| carried into sigma by
+    G tau, relative to max |sigma| -- 7.6e-5 on the narrowest channel of this draw, measured 0.9x)."""
     ps = inputs.sweep_channel_params(512, 3)
     nys = [q.pop("ny") for q in ps]
     with lbnlm.Channels(4, nys, ps, "f32", stream=stream) as sim:
@@ -207,5 +208,8 @@ def test_full_size_sweep_sampled_channels_match_oracle(stream):
         oracle.run(ps[c], st, 2000, nthreads=8)
         u_o, s_o, _ = oracle.fields(ps[c], st)
         u_g, s_g, _ = fields[c]
-        print(f"ny {nys[c]}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e}")
-        assert rel(u_g, u_o) < 1e-5 and rel(s_g, s_o) < 2e-4
+        q = ps[c]
+        floor = q["G_inf"] * q["theta"] * q["tau0"] * float(np.spacing(np.float32(np.abs(u_o).max()))) / np.abs(s_o).max()
+        print(f"ny {nys[c]} theta {q['theta']:.0f}: u {rel(u_g, u_o):.2e}, sigma {rel(s_g, s_o):.2e} "
+              f"= {rel(s_g, s_o) / floor:.2f} x floor {floor:.2e}")
+        assert rel(u_g, u_o) < 1e-5 and rel(s_g, s_o) < max(1e-5, 1.5 * floor)
