@@ -35,6 +35,11 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                      paper's scheme to O(H^-2) and against Eq. (maxwellpoiseuille), Newtonian
                      cross-check (a Delta eta D stress acts as the viscosity Delta eta)
                      (tests/test_oracle_schemes.py)
+    relaxation       tau(rho): homogeneous Couette shear at a uniform density equals the Sec. III A
+    extensions       closed form at tau exp(beta (rho - rho_ref)/rho_ref); fluidity memory: the
+                     backward-Euler recursion against its closed form, steady states unchanged,
+                     start-up stress overshoot with a long memory
+                     (tests/test_oracle_relaxation_models.py)
 """
 from __future__ import annotations
 
@@ -66,7 +71,8 @@ class OrcParams(ctypes.Structure):
                 ("tau0", ctypes.c_double), ("theta", ctypes.c_double), ("gamma_c", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("stress_mode", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double), ("top_wall", ctypes.c_int),
-                ("scheme", ctypes.c_int), ("u_wall", ctypes.c_double)]
+                ("scheme", ctypes.c_int), ("u_wall", ctypes.c_double), ("beta_rho", ctypes.c_double),
+                ("rho_ref", ctypes.c_double), ("tau_f", ctypes.c_double)]
 
 
 SCHEMES = {"paper": 0, "generalized_newtonian": 1, "stress_divergence": 2}
@@ -88,12 +94,14 @@ def _load():
         lib.orc_stress_gauss.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D]
         lib.orc_stress_step.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D, _D]
         lib.orc_init.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
-        lib.orc_run.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_int, ctypes.c_int, _D, _D, _D,
+        lib.orc_run.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_int, ctypes.c_int, _D, _D, _D, _D,
                                 ctypes.c_long, ctypes.c_int]
         lib.orc_fields.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_int, ctypes.c_int, _D, _D, _D,
-                                   _D, _D, _D]
+                                   _D, _D, _D, _D]
         lib.orc_node_intermediates.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_int, ctypes.c_int,
-                                               _D, _D, _D, _D]
+                                               _D, _D, _D, _D, _D]
+        lib.orc_fluidity_step.argtypes = [ctypes.c_double] * 3
+        lib.orc_fluidity_step.restype = ctypes.c_double
         lib.orc_fallback_count.restype = ctypes.c_long
         _lib = lib
     return _lib
@@ -132,7 +140,8 @@ def to_params(p, nx: int | None = None) -> OrcParams:
     stress_mode and optionally x_mode ("periodic" or "gpbc"; GPBC needs nx), top_wall
     ("bounce_back" or "moving": planar Couette flow with a Zou-He wall on the last row) and
     u_wall; scheme ("paper", "generalized_newtonian" or "stress_divergence", the comparison
-    schemes of Sec. II C)."""
+    schemes of Sec. II C); beta_rho, rho_ref (density-dependent tau) and tau_f (memory time of the
+    fluidity 1/tau_M), the relaxation-time extensions of the paper's outlook (off by default)."""
     get = (lambda k, d=None: p.get(k, d)) if isinstance(p, dict) else (lambda k, d=None: getattr(p, k, d))
     gpbc = get("x_mode", "periodic") == "gpbc"
     rin, rout = gpbc_density_offsets(p, nx) if gpbc else (0.0, 0.0)
@@ -140,7 +149,8 @@ def to_params(p, nx: int | None = None) -> OrcParams:
                      float(get("tau0", 0.0)), float(get("theta", 0.0)), float(get("gamma_c", np.inf)),
                      float(get("rho0", 1.0)), int(get("stress_mode", 0)), 1 if gpbc else 0, rin, rout,
                      1 if get("top_wall", "bounce_back") == "moving" else 0,
-                     SCHEMES[get("scheme", "paper")], float(get("u_wall", 0.0)))
+                     SCHEMES[get("scheme", "paper")], float(get("u_wall", 0.0)),
+                     float(get("beta_rho", 0.0)), float(get("rho_ref", 1.0)), float(get("tau_f", 0.0)))
 
 
 # --- per-node functions ---------------------------------------------------------------------
@@ -205,12 +215,22 @@ def fallback_count() -> int:
 
 # --- whole-grid state -----------------------------------------------------------------------
 
+def fluidity_step(phi_old: float, phi_ss: float, tau_f: float) -> float:
+    """One backward-Euler step of the fluidity memory d phi/dt = (phi_ss - phi)/tau_f (dt = 1)."""
+    return _load().orc_fluidity_step(phi_old, phi_ss, tau_f)
+
+
 @dataclass
 class State:
     dev: np.ndarray    # [9, ny, nx]  n*_i - w_i
     drho: np.ndarray   # [ny, nx]
     sig: np.ndarray    # [3, ny, nx]
     step: int = 0
+    phi: np.ndarray = None  # [ny, nx] fluidity 1/tau_M of the memory model (0: not yet set)
+
+    def __post_init__(self):
+        if self.phi is None:
+            self.phi = np.zeros(self.drho.shape)
 
     @property
     def shape(self):
@@ -222,7 +242,7 @@ class State:
         return self.dev + WEIGHTS[:, None, None]
 
     def copy(self) -> "State":
-        return State(self.dev.copy(), self.drho.copy(), self.sig.copy(), self.step)
+        return State(self.dev.copy(), self.drho.copy(), self.sig.copy(), self.step, self.phi.copy())
 
 
 def init_state(rho: np.ndarray) -> State:
@@ -256,7 +276,7 @@ def run(params, st: State, nsteps: int, nthreads: int = 1) -> State:
     """Advance ``st`` in place by ``nsteps`` steps; returns it."""
     ny, nx = st.shape
     pp = to_params(params, nx)
-    rc = _load().orc_run(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho), _p(st.sig),
+    rc = _load().orc_run(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho), _p(st.sig), _p(st.phi),
                          int(nsteps), int(nthreads))
     if rc != 0:
         raise ValueError("oracle rejected the grid or parameters")
@@ -272,7 +292,7 @@ def fields(params, st: State):
     sg = np.zeros((ny, nx, 4))
     rho = np.zeros((ny, nx))
     pp = to_params(params, nx)
-    rc = _load().orc_fields(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho), _p(st.sig),
+    rc = _load().orc_fields(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho), _p(st.sig), _p(st.phi),
                             _p(u), _p(sg), _p(rho))
     if rc != 0:
         raise ValueError("oracle rejected the grid or parameters")
@@ -285,7 +305,7 @@ def intermediates(params, st: State) -> np.ndarray:
     out = np.zeros((ny, nx, 9))
     pp = to_params(params, nx)
     rc = _load().orc_node_intermediates(ctypes.byref(pp), nx, ny, _p(st.dev), _p(st.drho),
-                                        _p(st.sig), _p(out))
+                                        _p(st.sig), _p(st.phi), _p(out))
     if rc != 0:
         raise ValueError("oracle rejected the grid or parameters")
     return out

@@ -74,6 +74,20 @@
  *     j = J0 + (f^ex + f^nN)/2 for n^eq and the force terms of Eq. (bodyforce) with f^ex + f^nN.
  *     (A divergence lagged by one step went unstable once Sigma^nN acted as a negative viscosity
  *     beyond -0.3 eta^N, and oscillated from step to step near tau_LB = 1/2.)
+ *
+ * Extensions of the relaxation time that the paper leaves for further study (Sec. III A: tau_M
+ * influenced by earlier times, the fluidity models; conclusions: tau depending on the local
+ * density).  The paper fixes neither form; the oracle takes these, both off by default:
+ *   - tau(rho) = tau exp(beta_rho (rho_hat - rho_ref) / rho_ref), with rho_hat = R0 - drho(t-1)
+ *     the hydrodynamic density known before the stress (explicit order; equal to rho_eq - drho(t)
+ *     in a steady state);
+ *   - fluidity memory: phi = 1/tau_M relaxes towards its instantaneous value of Eq. (nlmaxwell),
+ *     phi_ss = 1/tau + II_D^{1/2}/gamma_c, with the memory time tau_f:  d phi/dt = (phi_ss - phi)/
+ *     tau_f, stepped by backward Euler, phi(t) = (tau_f phi(t-1) + phi_ss(t)) / (tau_f + 1), i.e.
+ *     phi(t) is an exponentially weighted history of phi_ss.  The state carries phi per node (0
+ *     before the first step: start from phi_ss).  With stress mode 1 this is the integral
+ *     generalized Maxwell model sigma(t) = int G(t,t') [-d_t' B(t,t')] dt' with
+ *     d_t G(t,t') = -G/tau_M(t) and a non-instantaneous tau_M.
  */
 #include <math.h>
 #include <stdint.h>
@@ -109,6 +123,9 @@ typedef struct {
     int top_wall;   /* 0: half-way bounce-back; 1: wall on row ny-1 moving with u_wall (Zou-He) */
     int scheme;     /* 0: the paper's forcing; 1: generalized Newtonian tau_LB; 2: div Sigma force */
     double u_wall;  /* tangential velocity of the moving wall                                   */
+    double beta_rho;/* density dependence tau(rho) = tau exp(beta_rho (rho - rho_ref)/rho_ref)   */
+    double rho_ref; /* reference density of tau(rho)                                             */
+    double tau_f;   /* memory time of the fluidity 1/tau_M (0: instantaneous, Eq. nlmaxwell)      */
 } orc_params;
 
 /* the body-force density of Eq. (rhoj) / Eq. (bodyforce): none in a pressure-driven channel */
@@ -357,7 +374,14 @@ typedef struct {
     double rho_eq_m1, u[2];/* density (minus 1) and velocity handed to n^eq           */
     double tau_lb;         /* relaxation time of this node's collision                */
     double snn[3];         /* Sigma^nN (xx, xy, yy)                                   */
+    double phi;            /* fluidity 1/tau_M after this step's memory update (tau_f > 0) */
 } node_result;
+
+/* One backward-Euler step of the fluidity memory: d phi/dt = (phi_ss - phi)/tau_f (dt = 1). */
+double orc_fluidity_step(double phi_old, double phi_ss, double tau_f) {
+    if (tau_f <= 0.0 || !(phi_old > 0.0)) return phi_ss;
+    return (tau_f * phi_old + phi_ss) / (tau_f + 1.0);
+}
 
 static inline long idx(int nx, int x, int y) { return (long)y * nx + x; }
 
@@ -404,7 +428,8 @@ static void stress_divergence(int nx, int ny, const double *snn, double *out) {
  * moments R0 / j and gradient velocity ug of every node, drho_prev and the carried stress. */
 static void node_update(const orc_params *p, int nx, int ny, int x, int y,
                         const double *R0m1, const double *j, const double *ug,
-                        const double *drho_prev, const double *sig_prev, node_result *r) {
+                        const double *drho_prev, const double *sig_prev, const double *phi_prev,
+                        node_result *r) {
     long N = (long)nx * ny, k = idx(nx, x, y);
     r->R0m1 = R0m1[k];
     r->j[0] = j[2 * k];
@@ -419,7 +444,18 @@ static void node_update(const orc_params *p, int nx, int ny, int x, int y,
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) II_D += 0.5 * D[a][b] * D[b][a];
     double tau = p->theta * p->tau0;
+    if (p->beta_rho != 0.0 && tau > 0.0) { /* tau(rho) of the node's hydrodynamic density */
+        double rho_hat = 1.0 + R0m1[k] - drho_prev[k];
+        tau *= exp(p->beta_rho * (rho_hat - p->rho_ref) / p->rho_ref);
+    }
     r->tau_M = orc_relaxation_time(tau, p->gamma_c, II_D);
+    r->phi = 0.0;
+    if (p->tau_f > 0.0 && tau > 0.0) { /* fluidity memory */
+        double inv_gc = isinf(p->gamma_c) ? 0.0 : 1.0 / p->gamma_c;
+        double phi_ss = 1.0 / tau + sqrt(II_D) * inv_gc;
+        r->phi = orc_fluidity_step(phi_prev[k], phi_ss, p->tau_f);
+        r->tau_M = 1.0 / r->phi;
+    }
     r->tau_lb = p->tau_lb;
     if (p->scheme == 1) {
         /* generalized Newtonian: a locally Newtonian fluid with the effective viscosity of the
@@ -616,10 +652,13 @@ static void work_free(orc_work *w) {
 
 static int valid_grid(int nx, int ny) { return nx >= 1 && ny >= 3; }
 
-/* The comparison schemes run with periodic x, bounce-back walls and stress mode 0. */
-static int valid_scheme(const orc_params *p) {
+/* The comparison schemes run with periodic x, bounce-back walls and stress mode 0, without the
+ * relaxation-time extensions; the fluidity memory needs its state array. */
+static int valid_scheme(const orc_params *p, const double *phi) {
+    if (p->tau_f < 0.0 || !(p->rho_ref > 0.0) || (p->tau_f > 0.0 && !phi)) return 0;
     if (p->scheme == 0) return 1;
     if (p->scheme != 1 && p->scheme != 2) return 0;
+    if (p->beta_rho != 0.0 || p->tau_f != 0.0) return 0;
     return p->stress_mode == 0 && p->boundary == 0 && p->top_wall == 0;
 }
 
@@ -636,7 +675,7 @@ static void moments_for_step(const orc_params *p, int nx, int ny, const double *
         for (int x = 0; x < nx; ++x) {
             long k = idx(nx, x, y);
             node_result r;
-            node_update(p, nx, ny, x, y, w->R0m1, w->j, w->ug, drho, sig, &r);
+            node_update(p, nx, ny, x, y, w->R0m1, w->j, w->ug, drho, sig, NULL, &r);
             w->snn[k] = r.snn[0];
             w->snn[N + k] = r.snn[1];
             w->snn[2 * N + k] = r.snn[2];
@@ -659,9 +698,9 @@ static void stress_force(const orc_params *p, const orc_work *w, long N, long k,
 
 /* Advance the state (dn_star, drho, sig) by nsteps steps in place.  Returns 0, or -1 on a bad
  * argument / allocation failure. */
-int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, double *sig,
+int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, double *sig, double *phi,
             long nsteps, int nthreads) {
-    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p)) return -1;
+    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p, phi)) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -679,7 +718,7 @@ int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, 
             for (int x = 0; x < nx; ++x) {
                 long k = idx(nx, x, y);
                 node_result r;
-                node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
+                node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, phi, &r);
                 double dneq[9], F[9], f[2];
                 stress_force(p, &w, N, k, &r, f);
                 orc_equilibrium_offset(r.rho_eq_m1, r.u[0], r.u[1], dneq);
@@ -690,6 +729,7 @@ int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, 
                     dn_star[i * N + k] = dni - (dni - dneq[i]) / r.tau_lb + F[i];
                 }
                 drho[k] = r.drho;
+                if (p->tau_f > 0.0) phi[k] = r.phi; /* (only this node reads its own phi) */
                 if (p->stress_mode == 1) {
                     sig[k] = r.sigma[0];
                     sig[N + k] = r.sigma[1];
@@ -708,8 +748,8 @@ int orc_run(const orc_params *p, int nx, int ny, double *dn_star, double *drho, 
  *   rho[y][x]    = hydrodynamic density rho_eq - delta rho(t)  (Eq. rhoj, reading C1).
  * The state is not modified. */
 int orc_fields(const orc_params *p, int nx, int ny, const double *dn_star, const double *drho,
-               const double *sig, double *u, double *sigma, double *rho) {
-    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p)) return -1;
+               const double *sig, const double *phi, double *u, double *sigma, double *rho) {
+    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p, phi)) return -1;
     long N = (long)nx * ny;
     orc_work w;
     if (work_alloc(&w, N)) { work_free(&w); return -1; }
@@ -719,7 +759,7 @@ int orc_fields(const orc_params *p, int nx, int ny, const double *dn_star, const
             long k = idx(nx, x, y);
             node_result r;
             double f[2];
-            node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
+            node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, phi, &r);
             stress_force(p, &w, N, k, &r, f);
             double rho_h = 1.0 + (r.rho_eq_m1 - r.drho);
             if (u) { u[2 * k] = r.j[0] / rho_h; u[2 * k + 1] = r.j[1] / rho_h; }
@@ -738,8 +778,8 @@ int orc_fields(const orc_params *p, int nx, int ny, const double *dn_star, const
 /* Diagnostic access to the per-node intermediates of one update (kappa, tau_M, drho, S),
  * used by tests: out[y][x][9] = kxx, kxy, kyx, kyy, tau_M, drho, S, rho_eq, tau_LB of the node. */
 int orc_node_intermediates(const orc_params *p, int nx, int ny, const double *dn_star,
-                           const double *drho, const double *sig, double *out) {
-    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p)) return -1;
+                           const double *drho, const double *sig, const double *phi, double *out) {
+    if (!valid_grid(nx, ny) || (p->stress_mode == 1 && !sig) || !valid_scheme(p, phi)) return -1;
     long N = (long)nx * ny;
     orc_work w;
     if (work_alloc(&w, N)) { work_free(&w); return -1; }
@@ -749,7 +789,7 @@ int orc_node_intermediates(const orc_params *p, int nx, int ny, const double *dn
             long k = idx(nx, x, y);
             node_result r;
             double f[2];
-            node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, &r);
+            node_update(p, nx, ny, x, y, w.R0m1, w.j, w.ug, drho, sig, phi, &r);
             stress_force(p, &w, N, k, &r, f);
             double *o = out + 9 * k;
             o[0] = r.kap[0]; o[1] = r.kap[1]; o[2] = r.kap[2]; o[3] = r.kap[3];
