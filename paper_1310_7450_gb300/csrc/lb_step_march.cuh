@@ -1,20 +1,21 @@
 // lb_step_march.cuh -- the fused lattice-Boltzmann step for wide channels: a TMA-fed row march.
 //
-// A CTA of W threads owns a strip of W columns (x0 .. x0+W-1) and marches through rows y0..y1-1
-// of one channel.  The post-collision populations of the previous step stream into a ring of K
+// A CTA owns a strip of CW columns (x0 .. x0+CW-1), NC adjacent columns per thread, and marches
+// through rows y0..y1-1 of one channel.  The post-collision populations of the previous step stream into a ring of K
 // shared-memory slots, one source row per slot: a single 3-D tensor-memory-access copy brings the
-// 9 direction planes of that row, columns x0-HP .. x0+W+HP-1 (HP = 16 bytes of halo on each side,
+// 9 direction planes of that row, columns x0-HP .. x0+CW+HP-1 (HP = 16 bytes of halo on each side,
 // so every copy starts on a 16-byte boundary).  The copies run K-2 rows ahead of the arithmetic
 // and complete on one mbarrier per slot.
 //
 // Per row y (one __syncthreads per row):
-//   1. moments (Eq. rhoj) of row y+1 for the W own columns and the two halo columns x0-1, x0+W,
+//   1. moments (Eq. rhoj) of row y+1 for the CW own columns and the two halo columns x0-1, x0+CW,
 //      pulled from slots y, y+1, y+2 (Eq. lbupdate, pull form; bounce-back at the walls,
 //      Sec. II B); the own populations stay in registers for the next row's collision;
 //      the gradient velocity j/R0 goes into a 4-row ring in shared memory;
-//   2. barrier; one thread (lane 0 of the last warp) refills the slot of row y with row y+K;
+//   2. barrier; one thread (the last lane) refills the slot of row y with row y+K;
 //   3. collision of row y: kappa by three-point differences from the velocity ring, the nlM
-//      stress, Sigma^nN, delta rho, n^eq, F_i (Eq. bodyforce), BGK; coalesced stores.
+//      stress, Sigma^nN, delta rho, n^eq, F_i (Eq. bodyforce), BGK; coalesced stores (with two
+//      columns per thread, 8-byte FP32 pairs and 4-byte BF16 pairs).
 // The periodic wrap of x is patched into the halo columns of the first and last strip with
 // plain loads.  Every mbarrier wait is bounded (MarchCtl::max_wait_ns, 2 s by default): on timeout
 // the CTA records LB_ETIMEOUT in the status word, drains its own copies (also bounded) and returns.
@@ -120,18 +121,73 @@ constexpr size_t march_smem_bytes() {
     return 128 /*barriers*/ + K * slot + (size_t)4 * (W + 2) * 2 * sizeof(C);
 }
 
+// Row loads and stores of NC adjacent values of one plane (8-byte vector accesses for two floats).
+template <typename C, int NC>
+__device__ __forceinline__ void load_cols(const C* p, C (&v)[NC]) {
+    if constexpr (NC == 2 && sizeof(C) == 4) {
+        const float2 q = *reinterpret_cast<const float2*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c] = p[c];
+    }
+}
+template <typename C, int NC>
+__device__ __forceinline__ void store_cols(C* p, const C (&v)[NC]) {
+    if constexpr (NC == 2 && sizeof(C) == 4) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) p[c] = v[c];
+    }
+}
+// Post-collision populations d + D of NC adjacent nodes (node index of the first in `node`): two
+// FP32 values per 8-byte store, two BF16 values (rounded to nearest) per 4-byte store; stochastic
+// rounding goes node by node through store_node.
+template <typename T, typename C, int NC>
+__device__ __forceinline__ void store_cols_pop(T* po, long long P, const C (&d)[NC][9], const C (&D)[NC][9], bool sr,
+                                               uint32_t key, uint32_t node) {
+    if constexpr (NC == 2 && std::is_same<T, float>::value) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            *reinterpret_cast<float2*>(po + (long long)i * P) = make_float2(d[0][i] + D[0][i], d[1][i] + D[1][i]);
+    } else {
+        if constexpr (NC == 2 && std::is_same<T, __nv_bfloat16>::value) {
+            if (!sr) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    *reinterpret_cast<__nv_bfloat162*>(po + (long long)i * P) =
+                        __floats2bfloat162_rn(d[0][i] + D[0][i], d[1][i] + D[1][i]);
+                return;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) store_node<T, C>(po + c, P, d[c], D[c], sr, key, node + (uint32_t)c);
+    }
+}
+
 // BND = 1: channel ends joined by the generalized periodic boundaries of Sec. II B, and a moving
 // Couette wall on the last row (Sec. IV C) if the channel has one; BND = 2: the moving wall only;
 // both applied where the populations are pulled (the same rules as the tile kernel's pull9).
 // BND = 0: periodic x and bounce-back walls only.
-template <typename T, typename C, int SMODE, int W, int K, int BND = 0>
-__global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUtensorMap tmap, const StepArgs<T, C> a,
-                                                  const MarchCtl ctl) {
+// CW columns per CTA, NC adjacent columns per thread (CW / NC threads).
+// Resident CTAs per SM the two-column kernel is compiled for: 7 caps it at 127 registers (no
+// spills), 14 warps per SM instead of 10 at its natural 155 (BF16 at 4096 x 4096: 73.8 GLUPS at 7,
+// 72.3 at 8, 69.0 at 5; its warps stall mostly on fixed-latency dependencies, which more warps hide).
+#ifndef LBK_MARCH_MINB2
+#define LBK_MARCH_MINB2 7
+#endif
+template <typename T, typename C, int SMODE, int CW, int NC, int K, int BND = 0>
+__global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step_march(const __grid_constant__ CUtensorMap tmap,
+                                                          const StepArgs<T, C> a, const MarchCtl ctl) {
+    constexpr int NT = CW / NC;                                      // threads per CTA
     constexpr int HP = MarchGeom<T>::HP;
-    constexpr int SW = W + 2 * HP;                                   // slot row width (elements)
+    constexpr int SW = CW + 2 * HP;                                  // slot row width (elements)
     constexpr size_t SLOT = ((size_t)9 * SW * sizeof(T) + 127) / 128 * 128;
     constexpr uint32_t TX = 9u * SW * sizeof(T);                     // bytes per copy
-    constexpr int UW = W + 2;                                         // velocity ring row width
+    constexpr int UW = CW + 2;                                       // velocity ring row width
+    static_assert(NT >= 64 && NT % 32 == 0, "the edge patchers and the issuing thread need two warps");
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);               // K mbarriers (<= 16)
@@ -145,8 +201,9 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
 
     __shared__ int s_bad;  // set by any thread whose bounded wait gave up; read after a barrier
     __shared__ C s_delta[2];  // BND == 1 with GPBC: rho_out - mean(x = 0), rho_in - mean(x = nx-1)
-    constexpr int TI = W - 32;  // the thread that issues the copies (lane 0 of the last warp;
-                                // warp 0 computes the halo columns)
+    constexpr int TI = NT - 1;  // the thread that issues the copies (last lane; warp 0 computes
+                                // the halo columns)
+    constexpr int TP = NT - 2;  // the thread that issues the L2 prefetches of residual steps
     if (t == 0) {
         s_bad = 0;
         if (BND == 1 && a.gcol != nullptr) {
@@ -181,8 +238,9 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         const int rbase = y0 - 2;                 // first source row of this item
         const int rlast = y1 + 1;                 // last source row
         const uint32_t L0 = nload;                // load index of row rbase
-        const bool left_edge = (x0 == 0), right_edge = (x0 + W == nx);
-        const int x = x0 + t;
+        const bool left_edge = (x0 == 0), right_edge = (x0 + CW == nx);
+        const int col0 = NC * t;                  // first own column (relative to x0)
+        const int x = x0 + col0;                  // its global column
 
         // index of the copy holding source row r, and the wait for it
         auto idx_of = [&](int r) -> uint32_t { return L0 + (uint32_t)(r - rbase); };
@@ -190,20 +248,20 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             const uint32_t i = idx_of(r);
             return mbar_wait(&bars[i % K], (i / K) & 1u, ctl.max_wait_ns);
         };
-        // periodic wrap: the edge strips' halo columns x0-2, x0-1 (left) or x0+W, x0+W+1 (right)
+        // periodic wrap: the edge strips' halo columns x0-2, x0-1 (left) or x0+CW, x0+CW+1 (right)
         // come from the other end of the row; threads 0..17 (left) and 32..49 (right) each own
         // one (direction, column) value, loaded two rows before it is patched into its slot
         const bool patcher = (left_edge && t < 18) || (right_edge && t >= 32 && t < 50);
         const int pi = left_edge && t < 18 ? (t >> 1) : ((t - 32) >> 1);             // direction
         const int pc = left_edge && t < 18 ? (nx - 2 + (t & 1)) : ((t - 32) & 1);     // global column
-        const int ps = left_edge && t < 18 ? (HP - 2 + (t & 1)) : (HP + W + ((t - 32) & 1));  // slot column
+        const int ps = left_edge && t < 18 ? (HP - 2 + (t & 1)) : (HP + CW + ((t - 32) & 1));  // slot column
         auto patch_load = [&](int r) -> T {
             return (r >= 0 && r < ny && r <= rlast) ? a.pin[9 * ctl.base + (long long)pi * ctl.plane + (long long)r * nx + pc] : T(0);
         };
         auto patch_store = [&](int r, T v) {
             if (r >= 0 && r < ny && r <= rlast) const_cast<T*>(slot_ptr(idx_of(r)))[pi * SW + ps] = v;
         };
-        // pulled populations of node (col, r) from the slots (col relative to x0, may be -1 or W):
+        // pulled populations of node (col, r) from the slots (col relative to x0, may be -1 or CW):
         // direction i comes from source row r - cy_i, column col - cx_i
         auto pull = [&](int col, int r, C (&d)[9]) {
             const T* s0 = slot_ptr(idx_of(r)) + HP + col;
@@ -269,16 +327,19 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             u[0] = ux;
             u[1] = uy;
         };
-        auto moments_row = [&](int r, C (&d)[9], C& dR, C& jx, C& jy) {
-            // own column, then the two halo columns (threads 0 and 1)
+        auto moments_row = [&](int r, C (&d)[NC][9], C (&dR)[NC], C (&jx)[NC], C (&jy)[NC]) {
+            // own columns, then the two halo columns (threads 0 and 1)
             if (r >= 0 && r < ny) {
-                C ux, uy;
-                pull(t, r, d);
-                gradient_velocity<C>(d, P.gx, dR, jx, jy, ux, uy);
-                put_u(r, t, ux, uy);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    C ux, uy;
+                    pull(col0 + c, r, d[c]);
+                    gradient_velocity<C>(d[c], P.gx, dR[c], jx[c], jy[c], ux, uy);
+                    put_u(r, col0 + c, ux, uy);
+                }
                 if (t < 2) {  // the two halo columns, on lanes 0 and 1 of one warp (one pass)
-                    const int col = t == 0 ? -1 : W;
-                    C dh[9], hR, hx, hy;
+                    const int col = t == 0 ? -1 : CW;
+                    C dh[9], hR, hx, hy, ux, uy;
                     pull(col, r, dh);
                     gradient_velocity<C>(dh, P.gx, hR, hx, hy, ux, uy);
                     put_u(r, col, ux, uy);
@@ -294,11 +355,11 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             for (int r = rbase; r < rbase + K && r <= rlast; ++r) issue(idx_of(r), x0, r);
         }
         nload = L0 + (uint32_t)(rlast - rbase + 1);
-        // residual partials (F_RESID) of this thread's column, in the arithmetic type (a few
-        // hundred rows at most); the block reduction below runs in double
+        // residual partials (F_RESID / F_MON) of this thread's columns, in the arithmetic type (a
+        // few hundred rows at most); the block reduction below runs in double
         C r_du2 = C(0), r_u2 = C(0), r_ux = C(0), r_umax2 = C(0);
-        C dcur[9], dnext[9];
-        C dRc = 0, jxc = 0, jyc = 0, dRn = 0, jxn = 0, jyn = 0;
+        C dcur[NC][9], dnext[NC][9];
+        C dRc[NC], jxc[NC], jyc[NC], dRn[NC], jxn[NC], jyn[NC];
         bool ok = true;
         for (int r = rbase; r <= rbase + 5; ++r) ok &= wait_row(r);
         if (!ok) s_bad = 1;
@@ -311,14 +372,16 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         __syncthreads();
         if (s_bad) { bad = true; break; }
         {
-            C dtmp[9], a0, a1, a2;
+            C dtmp[NC][9], a0[NC], a1[NC], a2[NC];
             moments_row(y0 - 1, dtmp, a0, a1, a2);
             if (y0 == 0) moments_row(2, dtmp, a0, a1, a2);
         }
         moments_row(y0, dcur, dRc, jxc, jyc);
         // the stored flow-induced density, loaded two rows ahead of its use
-        C drho_next = a.drho[ctl.base + (long long)y0 * nx + x];
-        C drho_next2 = (y0 + 1 < y1) ? a.drho[ctl.base + (long long)(y0 + 1) * nx + x] : C(0);
+        const C* drow = a.drho + ctl.base + x;
+        C drho_next[NC], drho_next2[NC];
+        load_cols<C, NC>(drow + (long long)y0 * nx, drho_next);
+        if (y0 + 1 < y1) load_cols<C, NC>(drow + (long long)(y0 + 1) * nx, drho_next2);
         // on residual steps the saved velocity of each row is prefetched the same way, and one
         // thread brings the delta rho and saved-velocity rows into L2 four rows before their
         // register loads (a residual step reads 16 B more per node than a plain one, and the
@@ -327,24 +390,25 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
         const bool mon = (a.flags & (F_RESID | F_MON)) != 0;
         const C* upx = a.uprev + 2 * ctl.base + x;
         const C* upy = upx + ctl.plane;
-        constexpr int TP = 32;  // the thread that issues the L2 prefetches (lane 0 of warp 1)
         auto prefetch_rows = [&](int r) {  // thread TP, residual steps, rows of this item only
             if (r < y1) {
                 const long long o = (long long)r * nx + x0;
-                prefetch_l2(a.drho + ctl.base + o, W * sizeof(C));
-                prefetch_l2(a.uprev + 2 * ctl.base + o, W * sizeof(C));
-                prefetch_l2(a.uprev + 2 * ctl.base + ctl.plane + o, W * sizeof(C));
+                prefetch_l2(a.drho + ctl.base + o, CW * sizeof(C));
+                prefetch_l2(a.uprev + 2 * ctl.base + o, CW * sizeof(C));
+                prefetch_l2(a.uprev + 2 * ctl.base + ctl.plane + o, CW * sizeof(C));
             }
         };
-        if (resid && t == TP)
-            for (int r = y0 + 2; r < y0 + 6; ++r) prefetch_rows(r);
-        C upx_next = C(0), upy_next = C(0), upx_next2 = C(0), upy_next2 = C(0);
+        C upx_next[NC], upy_next[NC], upx_next2[NC], upy_next2[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) upx_next[c] = upy_next[c] = upx_next2[c] = upy_next2[c] = C(0);
         if (resid) {
-            upx_next = upx[(long long)y0 * nx];
-            upy_next = upy[(long long)y0 * nx];
+            if (t == TP)
+                for (int r = y0 + 2; r < y0 + 6; ++r) prefetch_rows(r);
+            load_cols<C, NC>(upx + (long long)y0 * nx, upx_next);
+            load_cols<C, NC>(upy + (long long)y0 * nx, upy_next);
             if (y0 + 1 < y1) {
-                upx_next2 = upx[(long long)(y0 + 1) * nx];
-                upy_next2 = upy[(long long)(y0 + 1) * nx];
+                load_cols<C, NC>(upx + (long long)(y0 + 1) * nx, upx_next2);
+                load_cols<C, NC>(upy + (long long)(y0 + 1) * nx, upy_next2);
             }
         }
         __syncthreads();
@@ -364,17 +428,25 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                 pv_b = patch_load(y + 6);
             }
             moments_row(y + 1, dnext, dRn, jxn, jyn);
-            const C drho_prev = drho_next;
-            drho_next = drho_next2;
-            if (y + 2 < y1) drho_next2 = a.drho[ctl.base + (long long)(y + 2) * nx + x];
-            const C upx_cur = upx_next, upy_cur = upy_next;
+            C drho_prev[NC], upx_cur[NC], upy_cur[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                drho_prev[c] = drho_next[c];
+                drho_next[c] = drho_next2[c];
+                upx_cur[c] = upx_next[c];
+                upy_cur[c] = upy_next[c];
+            }
+            if (y + 2 < y1) load_cols<C, NC>(drow + (long long)(y + 2) * nx, drho_next2);
             if (resid) {
                 if (t == TP) prefetch_rows(y + 6);
-                upx_next = upx_next2;
-                upy_next = upy_next2;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    upx_next[c] = upx_next2[c];
+                    upy_next[c] = upy_next2[c];
+                }
                 if (y + 2 < y1) {
-                    upx_next2 = upx[(long long)(y + 2) * nx];
-                    upy_next2 = upy[(long long)(y + 2) * nx];
+                    load_cols<C, NC>(upx + (long long)(y + 2) * nx, upx_next2);
+                    load_cols<C, NC>(upy + (long long)(y + 2) * nx, upy_next2);
                 }
             }
             __syncthreads();
@@ -384,77 +456,95 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
                 fence_proxy_async();
                 issue(idx_of(y + K), x0, y + K);
             }
-            // 3. collision of row y
+            // 3. collision of row y, node by node, then the row's stores
             {
-                const C* uc = uring + 2 * ((y & 3) * UW + t + 1);
-                const C ka = C(0.5) * (uc[2] - uc[-2]);
-                const C kc = C(0.5) * (uc[3] - uc[-1]);
-                C kb, ke;
-                const C* up = uring + 2 * (((y + 1) & 3) * UW + t + 1);
-                const C* um = uring + 2 * (((y + 3) & 3) * UW + t + 1);  // row y-1
-                if (y == 0) {
-                    const C* up2 = uring + 2 * (((y + 2) & 3) * UW + t + 1);
-                    kb = C(0.5) * (C(-3) * uc[0] + C(4) * up[0] - up2[0]);
-                    ke = C(0.5) * (C(-3) * uc[1] + C(4) * up[1] - up2[1]);
-                } else if (y == ny - 1) {
-                    const C* um2 = uring + 2 * (((y + 2) & 3) * UW + t + 1);  // row y-2
-                    kb = C(0.5) * (C(3) * uc[0] - C(4) * um[0] + um2[0]);
-                    ke = C(0.5) * (C(3) * uc[1] - C(4) * um[1] + um2[1]);
-                } else {
-                    kb = C(0.5) * (up[0] - um[0]);
-                    ke = C(0.5) * (up[1] - um[1]);
-                }
-                C so_xx = 0, so_xy = 0, so_yy = 0;
-                const long long pn = (long long)y * nx + x;
+                const long long pn = (long long)y * nx + x;  // first own node
+                C so_xx[NC], so_xy[NC], so_yy[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) so_xx[c] = so_xy[c] = so_yy[c] = C(0);
                 if (SMODE == 1) {
-                    const C* s3 = a.sig3 + 3 * ctl.base;
-                    so_xx = s3[pn];
-                    so_xy = s3[ctl.plane + pn];
-                    so_yy = s3[2 * ctl.plane + pn];
+                    const C* s3 = a.sig3 + 3 * ctl.base + pn;
+                    load_cols<C, NC>(s3, so_xx);
+                    load_cols<C, NC>(s3 + ctl.plane, so_xy);
+                    load_cols<C, NC>(s3 + 2 * ctl.plane, so_yy);
                 }
-                const NodeState<C> s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dRc, jxc, jyc, drho_prev, so_xx, so_xy, so_yy);
-                const C rho_h = C(1) + s.dReq - s.drho;
-                vbad |= !velocity_ok<C>(jxc, jyc, rho_h, a.guard);  // NaN or too fast
-                C D[9];
-                collide_node<C>(P, s, dcur, D);
+                C D[NC][9], sxx[NC], syy[NC], sxy[NC], drho_new[NC], urx[NC], ury[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int col = col0 + c;
+                    const C* uc = uring + 2 * ((y & 3) * UW + col + 1);
+                    const C ka = C(0.5) * (uc[2] - uc[-2]);
+                    const C kc = C(0.5) * (uc[3] - uc[-1]);
+                    C kb, ke;
+                    const C* up = uring + 2 * (((y + 1) & 3) * UW + col + 1);
+                    const C* um = uring + 2 * (((y + 3) & 3) * UW + col + 1);  // row y-1
+                    if (y == 0) {
+                        const C* up2 = uring + 2 * (((y + 2) & 3) * UW + col + 1);
+                        kb = C(0.5) * (C(-3) * uc[0] + C(4) * up[0] - up2[0]);
+                        ke = C(0.5) * (C(-3) * uc[1] + C(4) * up[1] - up2[1]);
+                    } else if (y == ny - 1) {
+                        const C* um2 = uring + 2 * (((y + 2) & 3) * UW + col + 1);  // row y-2
+                        kb = C(0.5) * (C(3) * uc[0] - C(4) * um[0] + um2[0]);
+                        ke = C(0.5) * (C(3) * uc[1] - C(4) * um[1] + um2[1]);
+                    } else {
+                        kb = C(0.5) * (up[0] - um[0]);
+                        ke = C(0.5) * (up[1] - um[1]);
+                    }
+                    const NodeState<C> s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dRc[c], jxc[c], jyc[c], drho_prev[c],
+                                                                  so_xx[c], so_xy[c], so_yy[c]);
+                    const C rho_h = C(1) + s.dReq - s.drho;
+                    vbad |= !velocity_ok<C>(jxc[c], jyc[c], rho_h, a.guard);  // NaN or too fast
+                    collide_node<C>(P, s, dcur[c], D[c]);
+                    sxx[c] = s.sxx;
+                    syy[c] = s.syy;
+                    sxy[c] = s.sxy;
+                    drho_new[c] = s.drho;
+                    urx[c] = ury[c] = C(0);
+                    if (a.flags & (F_SAVE_U | F_RESID | F_MON)) {
+                        const C ih = Arith<C>::div(C(1), rho_h);
+                        urx[c] = jxc[c] * ih;
+                        ury[c] = jyc[c] * ih;
+                        if (mon) {
+                            const C u2 = urx[c] * urx[c] + ury[c] * ury[c];
+                            if (resid) {
+                                const C dx_ = urx[c] - upx_cur[c], dy_ = ury[c] - upy_cur[c];
+                                r_du2 += dx_ * dx_ + dy_ * dy_;
+                            }
+                            r_u2 += u2;
+                            r_ux += urx[c];
+                            r_umax2 = fmax(r_umax2, u2);
+                        }
+                    }
+                }
                 T* po = a.pout + 9 * ctl.base + pn;
-                store_node<T, C>(po, ctl.plane, dcur, D, (a.flags & F_SR) != 0, a.sr_key, (uint32_t)pn);
-                a.drho[ctl.base + pn] = s.drho;
+                store_cols_pop<T, C, NC>(po, ctl.plane, dcur, D, (a.flags & F_SR) != 0, a.sr_key, (uint32_t)pn);
+                store_cols<C, NC>(a.drho + ctl.base + pn, drho_new);
                 if (SMODE == 1) {
-                    C* s3 = a.sig3 + 3 * ctl.base;
-                    s3[pn] = s.sxx;
-                    s3[ctl.plane + pn] = s.sxy;
-                    s3[2 * ctl.plane + pn] = s.syy;
+                    C* s3 = a.sig3 + 3 * ctl.base + pn;
+                    store_cols<C, NC>(s3, sxx);
+                    store_cols<C, NC>(s3 + ctl.plane, sxy);
+                    store_cols<C, NC>(s3 + 2 * ctl.plane, syy);
                 }
                 if (a.flags & F_STORE_SIGMA) {  // (the zz plane holds 0 from lb_create on)
-                    C* s4 = a.sig4 + 4 * ctl.base;
-                    s4[pn] = s.sxx;
-                    s4[ctl.plane + pn] = s.syy;
-                    s4[3 * ctl.plane + pn] = s.sxy;
+                    C* s4 = a.sig4 + 4 * ctl.base + pn;
+                    store_cols<C, NC>(s4, sxx);
+                    store_cols<C, NC>(s4 + ctl.plane, syy);
+                    store_cols<C, NC>(s4 + 3 * ctl.plane, sxy);
                 }
-                if (a.flags & (F_SAVE_U | F_RESID | F_MON)) {
-                    const C ih = Arith<C>::div(C(1), rho_h);
-                    const C urx = jxc * ih, ury = jyc * ih;
-                    C* up_ = a.uprev + 2 * ctl.base;
-                    if (mon) {
-                        const C u2 = urx * urx + ury * ury;
-                        if (resid) {
-                            const C dx_ = urx - upx_cur, dy_ = ury - upy_cur;
-                            r_du2 += dx_ * dx_ + dy_ * dy_;
-                        }
-                        r_u2 += u2;
-                        r_ux += urx;
-                        r_umax2 = fmax(r_umax2, u2);
-                    }
-                    if (a.flags & F_SAVE_U) {
-                        up_[pn] = urx;
-                        up_[ctl.plane + pn] = ury;
-                    }
+                if (a.flags & F_SAVE_U) {
+                    C* up_ = a.uprev + 2 * ctl.base + pn;
+                    store_cols<C, NC>(up_, urx);
+                    store_cols<C, NC>(up_ + ctl.plane, ury);
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 9; ++i) dcur[i] = dnext[i];
-            dRc = dRn; jxc = jxn; jyc = jyn;
+            for (int c = 0; c < NC; ++c) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) dcur[c][i] = dnext[c][i];
+                dRc[c] = dRn[c];
+                jxc[c] = jxn[c];
+                jyc[c] = jyn[c];
+            }
         }
         __syncthreads();  // every slot read of this item is done before the next item's copies
         if (!bad && mon) {
@@ -473,7 +563,7 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
             __syncthreads();
             if (t == 0) {
                 double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                for (int w = 0; w < W / 32; ++w) {
+                for (int w = 0; w < NT / 32; ++w) {
                     s0 += red[4 * w]; s1 += red[4 * w + 1]; s2 += red[4 * w + 2]; s3 = fmax(s3, red[4 * w + 3]);
                 }
                 double* o = a.partials + 4 * (long long)item;
@@ -500,26 +590,41 @@ __global__ void __launch_bounds__(W, 5) k_step_march(const __grid_constant__ CUt
 }  // namespace lbk
 
 namespace lbk {
-constexpr int kMarchW = 128;  // threads (= columns) per CTA
+constexpr int kMarchW = 128;  // columns per CTA (one strip)
 constexpr int kMarchK = 8;    // shared-memory row slots (copies run K-2 rows ahead)
+#ifndef LBK_MARCH_NC_BF16
+#define LBK_MARCH_NC_BF16 2
+#endif
+// Adjacent columns per thread.  BF16 storage moves 56 B per node against FP32's 92, so its step is
+// bound by instruction issue: two columns per thread share the per-row address, ring and loop
+// work and pack their stores into bf16x2 words (497 -> 366 instructions per node; with 7 CTAs per
+// SM 57.7 -> 73.8 GLUPS at 4096 x 4096).  The FP32 step is
+// bound by HBM and keeps one column per thread (two measured 4 % slower: a 64-thread CTA at 161
+// registers leaves 10 warps per SM to cover the memory latency).  The boundary variants keep one.
+template <typename T, int BND>
+constexpr int march_nc() { return (BND == 0 && std::is_same<T, __nv_bfloat16>::value) ? LBK_MARCH_NC_BF16 : 1; }
 
 template <typename T, typename C, int SMODE, int BND = 0>
 cudaError_t launch_step_march(const CUtensorMap& map, const StepArgs<T, C>& a, const MarchCtl& ctl, int grid,
                               cudaStream_t s) {
-    auto k = k_step_march<T, C, SMODE, kMarchW, kMarchK, BND>;
+    constexpr int NC = march_nc<T, BND>();
+    auto k = k_step_march<T, C, SMODE, kMarchW, NC, kMarchK, BND>;
     const size_t smem = march_smem_bytes<T, C, kMarchW, kMarchK>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    k<<<grid, kMarchW, smem, s>>>(map, a, ctl);
+    k<<<grid, kMarchW / NC, smem, s>>>(map, a, ctl);
     return cudaGetLastError();
 }
 
 template <typename T, typename C, int SMODE, int BND = 0>
 cudaError_t march_occupancy(int* blocks_per_sm) {
-    auto k = k_step_march<T, C, SMODE, kMarchW, kMarchK, BND>;
+    constexpr int NC = march_nc<T, BND>();
+    auto k = k_step_march<T, C, SMODE, kMarchW, NC, kMarchK, BND>;
     const size_t smem = march_smem_bytes<T, C, kMarchW, kMarchK>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kMarchW, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kMarchW / NC, smem);
 }
 }  // namespace lbk
