@@ -66,9 +66,12 @@ enum { LB_STRESS_INLM = 0, LB_STRESS_TIMESTEPPED = 1 };
  * LB_GRID_STRESS_DIVERGENCE feeds f^nN = div Sigma^nN (three-point differences of the same-time
  * stress of every node, Sigma^nN = sigma + (G_inf tau0 - eta^N) D) as a force density into
  * Eq. (rhoj) and the force terms of Eq. (bodyforce) instead of the stress line and the
- * flow-induced density (two launches per step).  Both have delta rho = 0. */
+ * flow-induced density (two launches per step).  Both have delta rho = 0.
+ * LB_GRID_RELAXATION_MODEL keeps the paper's scheme and enables the relaxation-time extensions of
+ * its outlook (lb_set_relaxation_model; off until set): FP64, FP32 or BF16, either stress mode,
+ * any boundary, tile kernel, not in lb_run_until_steady; one more plane per node (the fluidity). */
 enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2, LB_GRID_BF16_STOCHASTIC = 4, LB_GRID_NO_GRAPH = 8,
-       LB_GRID_GENERALIZED_NEWTONIAN = 16, LB_GRID_STRESS_DIVERGENCE = 32 };
+       LB_GRID_GENERALIZED_NEWTONIAN = 16, LB_GRID_STRESS_DIVERGENCE = 32, LB_GRID_RELAXATION_MODEL = 64 };
 
 typedef struct {
     int n_channels;   /* >= 1                                                              */
@@ -294,6 +297,18 @@ lb_status lb_mlp_gradients(lb_mlp *m, const float *x, const float *target, int b
 lb_status lb_mlp_train_step(lb_mlp *m, const float *x, const float *target, int batch, float lr, double *loss);
 lb_status lb_mlp_get_params(lb_mlp *m, float *host);        /* FP32 masters -> host [n_params]     */
 lb_status lb_mlp_set_params(lb_mlp *m, const float *host);  /* host [n_params] -> masters and BF16 */
+
+/* Relaxation-time extensions that the paper leaves for further study (its conclusions: the Maxwell
+ * time should depend on the local density; Sec. III A: a flow dependence of tau_M influenced by
+ * earlier times, as in the fluidity models).  The paper fixes neither form; this library takes
+ *   tau(rho) = tau exp(beta_rho (rho - rho_ref) / rho_ref), rho = R0 - delta rho(t-1) at the node,
+ *   d phi/dt = (phi_ss - phi) / tau_f for the fluidity phi = 1/tau_M, phi_ss = 1/tau(rho) +
+ *   II_D^{1/2}/gamma_c (Eq. nlmaxwell), stepped by backward Euler (tau_f = 0: Eq. nlmaxwell).
+ * For one channel (channel >= 0) or all (-1); rho_ref > 0, tau_f >= 0, all finite; LB_EINVAL
+ * otherwise or if the handle was created without LB_GRID_RELAXATION_MODEL.  Synchronises the
+ * stream.  The fluidity of every node is part of the checkpoint image and is cleared (unset:
+ * the next step starts from phi_ss) by lb_set_populations. */
+lb_status lb_set_relaxation_model(lb_handle *h, int channel, double beta_rho, double rho_ref, double tau_f);
 
 /* Limit of every bounded device-side wait of the row-march step kernel (the mbarrier waits for its
  * row copies), in seconds: 0 <= seconds <= 60, default 2.  0 makes each wait a single non-blocking

@@ -36,6 +36,14 @@ extern template cudaError_t launch_step_tile<double, float, 0>(const StepArgs<do
 extern template cudaError_t launch_step_tile<double, float, 1>(const StepArgs<double, float>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<float, double, 0>(const StepArgs<float, double>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<float, double, 1>(const StepArgs<float, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<double, double, 0, 3>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<double, double, 1, 3>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<float, float, 0, 3>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<float, float, 1, 3>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_step_tile<__nv_bfloat16, float, 0, 3>(const StepArgs<__nv_bfloat16, float>&, int, size_t,
+                                                                         cudaStream_t);
+extern template cudaError_t launch_step_tile<__nv_bfloat16, float, 1, 3>(const StepArgs<__nv_bfloat16, float>&, int, size_t,
+                                                                         cudaStream_t);
 extern template cudaError_t launch_step_tile<double, double, 0, 1>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<double, double, 0, 2>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<float, float, 0, 1>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
@@ -342,7 +350,10 @@ struct lb_handle {
     // device state
     void *popA = nullptr, *popB = nullptr, *drho = nullptr, *sig3 = nullptr, *sig4 = nullptr, *uprev = nullptr;
     void* snn = nullptr;  // stress-divergence scheme: Sigma^nN of the current step [3 planes]
-    int scheme = 0;       // 0: the paper's forcing; 1: generalized Newtonian; 2: div Sigma^nN force
+    void* phi = nullptr;  // relaxation-time extensions: fluidity 1/tau_M per node [plane]
+    int scheme = 0;       // 0: the paper's forcing; 1: generalized Newtonian; 2: div Sigma^nN force;
+                          // 3: the paper's forcing with the relaxation-time extensions
+    std::vector<double> beta_rho, rho_ref, tau_f;  // scheme 3, per channel
     void* chan = nullptr;
     WorkItem* items_d = nullptr;
     int* item_begin_d = nullptr;
@@ -439,7 +450,13 @@ std::vector<ChanParams<C>> make_chan(const lb_handle* h) {
         q.moving = h->moving ? 1 : 0;
         q.u_wall = (C)h->u_wall[c];
         q.scheme = h->scheme;
-        if (h->scheme != 0) {
+        q.rho_ref = C(1);
+        if (h->scheme == 3) {
+            q.beta_rho = (C)h->beta_rho[c];
+            q.rho_ref = (C)h->rho_ref[c];
+            q.tau_f = (C)h->tau_f[c];
+        }
+        if (h->scheme == 1 || h->scheme == 2) {
             // the comparison schemes of Sec. II C: no stress line and no flow-induced density
             q.k1 = C(0);
             q.kdr = C(0);
@@ -606,7 +623,11 @@ lb_status validate(const lb_grid* g, const lb_params* p, const lb_boundary* b) {
         (b->x_mode != LB_X_PERIODIC && b->x_mode != LB_X_GPBC))
         return fail(LB_EINVAL, "lb_create: walls must be LB_WALLS_BOUNCE_BACK or LB_WALLS_COUETTE and x_mode LB_X_PERIODIC or LB_X_GPBC%s");
     const bool gn = (g->flags & LB_GRID_GENERALIZED_NEWTONIAN) != 0, dv = (g->flags & LB_GRID_STRESS_DIVERGENCE) != 0;
-    if (gn && dv) return fail(LB_EINVAL, "lb_create: choose one comparison scheme%s");
+    const bool rx = (g->flags & LB_GRID_RELAXATION_MODEL) != 0;
+    if ((int)gn + (int)dv + (int)rx > 1)
+        return fail(LB_EINVAL, "lb_create: choose one comparison scheme, or the relaxation-time extensions%s");
+    if (rx && g->precision != LB_PREC_F64 && g->precision != LB_PREC_F32 && g->precision != LB_PREC_BF16)
+        return fail(LB_EINVAL, "lb_create: the relaxation-time extensions run in FP64, FP32 or BF16%s");
     if ((gn || dv) && (g->stress_mode != 0 || b->walls != LB_WALLS_BOUNCE_BACK || b->x_mode != LB_X_PERIODIC))
         return fail(LB_EINVAL, "lb_create: the comparison schemes run with stress mode 0, periodic x and bounce-back walls%s");
     if ((gn || dv) && g->precision != LB_PREC_F64 && g->precision != LB_PREC_F32 && g->precision != LB_PREC_BF16)
@@ -636,7 +657,7 @@ void free_dev(T*& p) {
 void release(lb_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    free_dev(h->popA); free_dev(h->popB); free_dev(h->drho); free_dev(h->sig3); free_dev(h->sig4); free_dev(h->snn);
+    free_dev(h->popA); free_dev(h->popB); free_dev(h->drho); free_dev(h->sig3); free_dev(h->sig4); free_dev(h->snn); free_dev(h->phi);
     free_dev(h->uprev); free_dev(h->chan); free_dev(h->items_d); free_dev(h->item_begin_d);
     free_dev(h->partials); free_dev(h->mon_d); free_dev(h->status_d); free_dev(h->base_d); free_dev(h->P_d);
     free_dev(h->node_off_d); free_dev(h->ny_d); free_dev(h->gx_d); free_dev(h->fields); free_dev(h->fconv);
@@ -691,6 +712,7 @@ StepArgs<T, C> base_args(lb_handle* h) {
     a.sig4 = (C*)h->sig4;
     a.uprev = (C*)h->uprev;
     a.snn = (C*)h->snn;
+    a.phi = (double*)h->phi;
     a.partials = h->partials;
     a.items = h->items_d;
     a.chan = (const ChanParams<C>*)h->chan;
@@ -741,6 +763,9 @@ template <typename T, typename C>
 cudaError_t launch(lb_handle* h, const StepArgs<T, C>& a) {
     const int n = (int)h->items.size();
     if constexpr (kSchemeTypes<T, C>) {
+        if (h->scheme == 3)
+            return h->smode == 0 ? launch_step_tile<T, C, 0, 3>(a, n, h->smem, h->stream)
+                                 : launch_step_tile<T, C, 1, 3>(a, n, h->smem, h->stream);
         if (h->scheme == 1) return launch_step_tile<T, C, 0, 1>(a, n, h->smem, h->stream);
         if (h->scheme == 2) {
             // stress divergence: Sigma^nN of every node of this step first, then the step (or the
@@ -1196,7 +1221,7 @@ lb_status lb_run_until_steady(lb_handle* h, double tol, long check_every, long m
     if (h->gpbc || h->moving)
         return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements periodic x and bounce-back walls only%s");
     if (h->scheme != 0)
-        return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements the paper's scheme only (step comparison schemes with lb_step)%s");
+        return fail(LB_EINVAL, "lb_run_until_steady: the sweep kernel implements the paper's model only (step the comparison schemes and the relaxation-time extensions with lb_step)%s");
     if (h->prec == LB_PREC_F64S_F32M || h->prec == LB_PREC_F32S_F64M)
         return fail(LB_EINVAL, "lb_run_until_steady: diagnostic precision mixes are not supported%s");
     // Segments of growing length (64, 256, 1024, ... check intervals): after each one the
@@ -1354,10 +1379,14 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     h->smode = grid->stress_mode;
     h->flags = grid->flags;
     h->scheme = (grid->flags & LB_GRID_GENERALIZED_NEWTONIAN) ? 1 : ((grid->flags & LB_GRID_STRESS_DIVERGENCE) ? 2 : 0);
+    if (grid->flags & LB_GRID_RELAXATION_MODEL) h->scheme = 3;
     h->tsize = with_types(h->prec, [](auto tt, auto tc) { LB_TYPES(tt, tc); (void)sizeof(C); return sizeof(T); });
     h->csize = with_types(h->prec, [](auto tt, auto tc) { LB_TYPES(tt, tc); (void)sizeof(T); return sizeof(C); });
     h->ny.assign(grid->ny, grid->ny + h->n_ch);
     h->params.assign(params, params + h->n_ch);
+    h->beta_rho.assign(h->n_ch, 0.0);
+    h->rho_ref.assign(h->n_ch, 1.0);
+    h->tau_f.assign(h->n_ch, 0.0);
     h->P.resize(h->n_ch); h->base.resize(h->n_ch); h->node_off.resize(h->n_ch);
     long long acc = 0, nodes = 0;
     for (int c = 0; c < h->n_ch; ++c) {
@@ -1392,6 +1421,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     LB_ALLOC(h->drho, h->planes * h->csize);
     if (h->smode == 1) LB_ALLOC(h->sig3, 3 * h->planes * h->csize);
     if (h->scheme == 2) LB_ALLOC(h->snn, 3 * h->planes * h->csize);
+    if (h->scheme == 3) LB_ALLOC(h->phi, h->planes * sizeof(double));  // FP64 in every precision
     if (h->flags & LB_GRID_STORE_SIGMA) LB_ALLOC(h->sig4, 4 * h->planes * h->csize);
     LB_ALLOC(h->uprev, 2 * h->planes * h->csize);
     LB_ALLOC(h->chan, h->n_ch * (h->csize == 8 ? sizeof(ChanParams<double>) : sizeof(ChanParams<float>)));
@@ -1454,6 +1484,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     ok &= cudaMemsetAsync(h->uprev, 0, 2 * h->planes * h->csize, h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(h->popB, 0, 9 * h->planes * h->tsize, h->stream) == cudaSuccess;
     if (h->sig4) ok &= cudaMemsetAsync(h->sig4, 0, 4 * h->planes * h->csize, h->stream) == cudaSuccess;
+    if (h->phi) ok &= cudaMemsetAsync(h->phi, 0, h->planes * sizeof(double), h->stream) == cudaSuccess;
     if (!ok) { cudaFree(ic_d); return bail(cuda_fail(cudaGetLastError(), "lb_create: table upload")); }
     long long maxn = 0;
     for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
@@ -1474,6 +1505,30 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
 }
 
 void lb_destroy(lb_handle* h) { release(h); }
+
+lb_status lb_set_relaxation_model(lb_handle* h, int channel, double beta_rho, double rho_ref, double tau_f) {
+    if (!h || channel < -1 || channel >= h->n_ch || !std::isfinite(beta_rho) || !std::isfinite(rho_ref) ||
+        !(rho_ref > 0.0) || !std::isfinite(tau_f) || tau_f < 0.0)
+        return fail(LB_EINVAL, "lb_set_relaxation_model: bad handle, channel or parameter%s");
+    if (h->scheme != 3) return fail(LB_EINVAL, "lb_set_relaxation_model: the handle was created without LB_GRID_RELAXATION_MODEL%s");
+    for (int c = 0; c < h->n_ch; ++c)
+        if (channel < 0 || c == channel) {
+            h->beta_rho[c] = beta_rho;
+            h->rho_ref[c] = rho_ref;
+            h->tau_f[c] = tau_f;
+        }
+    // the whole channel table again (its body forces and wall velocities are the host's current
+    // ones), after the work already queued that reads the old table
+    LB_CK(cudaStreamSynchronize(h->stream));
+    if (h->csize == 8) {
+        auto v = make_chan<double>(h);
+        LB_CK(cudaMemcpy(h->chan, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice));
+    } else {
+        auto v = make_chan<float>(h);
+        LB_CK(cudaMemcpy(h->chan, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice));
+    }
+    return LB_OK;
+}
 
 lb_status lb_set_wait_limit(lb_handle* h, double seconds) {
     if (!h || !(seconds >= 0.0) || seconds > 60.0) return fail(LB_EINVAL, "lb_set_wait_limit: need 0 <= seconds <= 60%s");
@@ -1640,6 +1695,7 @@ lb_status lb_set_populations(lb_handle* h, const double* n, const double* drho, 
             LB_CK(cudaMemsetAsync(h->sig3, 0, 3 * h->planes * h->csize, h->stream));
         }
     }
+    if (h->phi) LB_CK(cudaMemsetAsync(h->phi, 0, h->planes * sizeof(double), h->stream));  // fluidity unset
     LB_CK(cudaStreamSynchronize(h->stream));
     h->uprev_state = -10;
     return LB_OK;
@@ -1683,6 +1739,7 @@ struct StateHeader {
     int64_t step, planes;
     int32_t n_ch, nx, prec, smode;
     uint64_t ny_hash;  // FNV-1a of the per-channel ny list: the image's channel split
+    int32_t scheme, pad_;  // the planes an image carries depend on the scheme
 };
 constexpr uint64_t kMagic = 0x4d4c4e2d424c6772ull;
 constexpr uint64_t kStateVersion = 2;
@@ -1702,12 +1759,14 @@ size_t lb_state_bytes(const lb_handle* h) {
     if (!h) return 0;
     size_t b = sizeof(StateHeader) + 9 * h->planes * h->tsize + h->planes * h->csize;
     if (h->smode == 1) b += 3 * h->planes * h->csize;
+    if (h->phi) b += h->planes * sizeof(double);
     return b;
 }
 
 lb_status lb_get_state(lb_handle* h, void* buf, size_t bytes) {
     if (!h || !buf || bytes < lb_state_bytes(h)) return fail(LB_EINVAL, "lb_get_state: bad buffer%s");
-    StateHeader hd{kMagic, kStateVersion, h->step, h->planes, h->n_ch, h->nx, h->prec, h->smode, ny_list_hash(h->ny)};
+    StateHeader hd{kMagic, kStateVersion, h->step, h->planes, h->n_ch, h->nx, h->prec, h->smode, ny_list_hash(h->ny),
+                   h->scheme, 0};
     char* p = (char*)buf;
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -1716,6 +1775,8 @@ lb_status lb_get_state(lb_handle* h, void* buf, size_t bytes) {
     LB_CK(cudaMemcpyAsync(p, h->drho, h->planes * h->csize, cudaMemcpyDeviceToHost, h->stream));
     p += h->planes * h->csize;
     if (h->smode == 1) LB_CK(cudaMemcpyAsync(p, h->sig3, 3 * h->planes * h->csize, cudaMemcpyDeviceToHost, h->stream));
+    if (h->smode == 1) p += 3 * h->planes * h->csize;
+    if (h->phi) LB_CK(cudaMemcpyAsync(p, h->phi, h->planes * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
@@ -1726,7 +1787,7 @@ lb_status lb_set_state(lb_handle* h, const void* buf, size_t bytes) {
     std::memcpy(&hd, buf, sizeof hd);
     if (hd.magic != kMagic || hd.version != kStateVersion)
         return fail(LB_EINVAL, "lb_set_state: not a state image of this library version%s");
-    if (hd.planes != h->planes || hd.n_ch != h->n_ch || hd.nx != h->nx || hd.prec != h->prec ||
+    if (hd.planes != h->planes || hd.n_ch != h->n_ch || hd.nx != h->nx || hd.prec != h->prec || hd.scheme != h->scheme ||
         hd.smode != h->smode || hd.ny_hash != ny_list_hash(h->ny))
         return fail(LB_EINVAL, "lb_set_state: image does not match this handle's grid or channel split%s");
     const char* p = (const char*)buf + sizeof hd;
@@ -1735,6 +1796,8 @@ lb_status lb_set_state(lb_handle* h, const void* buf, size_t bytes) {
     LB_CK(cudaMemcpyAsync(h->drho, p, h->planes * h->csize, cudaMemcpyHostToDevice, h->stream));
     p += h->planes * h->csize;
     if (h->smode == 1) LB_CK(cudaMemcpyAsync(h->sig3, p, 3 * h->planes * h->csize, cudaMemcpyHostToDevice, h->stream));
+    if (h->smode == 1) p += 3 * h->planes * h->csize;
+    if (h->phi) LB_CK(cudaMemcpyAsync(h->phi, p, h->planes * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     // a restored state starts healthy: the per-channel status word and the sticky flags are
     // cleared, so rolling back to a good image after an instability steps every channel again
     LB_CK(cudaMemsetAsync(h->status_d, 0, sizeof(int) * h->n_ch, h->stream));

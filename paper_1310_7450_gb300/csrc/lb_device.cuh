@@ -122,6 +122,9 @@ struct ChanParams {
     C u_wall;   // tangential velocity of the moving wall (moving == 1)
     C gn_a;     // scheme 1: tau_LB(gdot) = gn_b + gn_a tau_M, gn_a = G_inf / (rho0 c_s^2)
     C gn_b;     //           gn_b = 1/2 + eta_inf / (rho0 c_s^2)  (Eq. taulb with eta_eff)
+    C beta_rho; // scheme 3: tau(rho) = tau exp(beta_rho (rho - rho_ref) / rho_ref)
+    C rho_ref;
+    C tau_f;    // scheme 3: memory time of the fluidity 1/tau_M (0: Eq. nlmaxwell, instantaneous)
 };
 
 struct WorkItem {
@@ -157,6 +160,8 @@ struct StepArgs {
     C* __restrict__ frho;          //   rho [node]
     double* __restrict__ partials; // residual partials [item][4]
     C* __restrict__ snn;           // scheme 2: Sigma^nN (xx, xy, yy) of this step [3 planes]
+    double* __restrict__ phi;      // scheme 3: fluidity 1/tau_M of the last step [plane] (0: unset),
+                                   // FP64 in every precision (see relaxation_time_ext)
     const WorkItem* __restrict__ items;
     const ChanParams<C>* __restrict__ chan;
     int* __restrict__ status;      // per channel: 0 stable, 1 unstable
@@ -182,6 +187,7 @@ template <typename C> struct Arith;
 template <> struct Arith<double> {
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
 };
 #ifdef LBK_FP32_IEEE
 // Compile-time alternative: correctly rounded FP32 division and square root (IEEE round to
@@ -189,6 +195,7 @@ template <> struct Arith<double> {
 template <> struct Arith<float> {
     static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
     static __device__ __forceinline__ float sqrt(float x) { return __fsqrt_rn(x); }
+    static __device__ __forceinline__ float exp(float x) { return expf(x); }
 };
 #else
 template <> struct Arith<float> {
@@ -203,6 +210,7 @@ template <> struct Arith<float> {
         asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
         return x >= 1.17549435e-38f ? x * r : 0.f;
     }
+    static __device__ __forceinline__ float exp(float x) { return expf(x); }
 };
 #endif
 
@@ -286,15 +294,22 @@ struct NodeState {
     C ux, uy;          // velocity handed to n^eq and F_i: j / rho_eq
 };
 
-template <typename C, int SMODE>
+// TAUM = true: the relaxation time comes in as tau_M_in (the relaxation-time extensions of
+// scheme 3) instead of Eq. (nlmaxwell) with the channel's tau.
+template <typename C, int SMODE, bool TAUM = false>
 __device__ __forceinline__ NodeState<C> constitutive(const ChanParams<C>& P, C ka, C kb, C kc, C ke,
                                                      C dR, C jx, C jy, C drho_prev,
-                                                     C s_old_xx, C s_old_xy, C s_old_yy) {
+                                                     C s_old_xx, C s_old_xy, C s_old_yy, C tau_M_in = C(0)) {
     NodeState<C> r;
     const C Dxx = C(2) * ka, Dxy = kb + kc, Dyy = C(2) * ke;
-    const C II = C(0.5) * (Dxx * Dxx + C(2) * Dxy * Dxy + Dyy * Dyy);  // (1/2) tr D^2
-    // tau = 0 (Newtonian) gives tau_M = 0, alpha = 0 and a zero right-hand side, so sigma = 0
-    const C tau_M = Arith<C>::div(P.tau, C(1) + P.tau * Arith<C>::sqrt(II) * P.inv_gc);
+    C tau_M;
+    if constexpr (TAUM) {
+        tau_M = tau_M_in;
+    } else {
+        const C II = C(0.5) * (Dxx * Dxx + C(2) * Dxy * Dxy + Dyy * Dyy);  // (1/2) tr D^2
+        // tau = 0 (Newtonian) gives tau_M = 0, alpha = 0 and a zero right-hand side, so sigma = 0
+        tau_M = Arith<C>::div(P.tau, C(1) + P.tau * Arith<C>::sqrt(II) * P.inv_gc);
+    }
     {
         if (SMODE == 0) {
             const C gt = P.G * tau_M;
@@ -343,6 +358,35 @@ __device__ __forceinline__ NodeState<C> constitutive_gn(const ChanParams<C>& P, 
     r.uy = jy * inv;
     *omega = Arith<C>::div(C(1), P.gn_b + P.gn_a * tau_M);
     return r;
+}
+
+// Scheme 3, the relaxation-time extensions of the paper's outlook: the Maxwell time at the node's
+// hydrodynamic density, tau(rho) = tau exp(beta_rho (rho_hat - rho_ref)/rho_ref) with rho_hat =
+// R0 - delta rho(t-1) (the density known before the stress), and a fluidity phi = 1/tau_M that
+// relaxes towards Eq. (nlmaxwell), phi_ss = 1/tau + II_D^{1/2}/gamma_c, with memory time tau_f
+// (backward Euler: phi = (tau_f phi_old + phi_ss)/(tau_f + 1); phi_old = 0 means unset: phi_ss).
+// Returns tau_M; *phi receives the new fluidity (0 without memory).  The fluidity and its recursion
+// are FP64 in every precision: each step moves phi by 1/(tau_f + 1) of its distance to phi_ss, and
+// an FP32 phi would drop those increments once they fall below half a unit in its last place,
+// stalling up to (tau_f + 1) ulp / 2 away from phi_ss (1e-4 relative at tau_f = 2000).
+template <typename C>
+__device__ __forceinline__ C relaxation_time_ext(const ChanParams<C>& P, C ka, C kb, C kc, C ke, C dR, C drho_prev,
+                                                 double phi_old, double* phi) {
+    C tau = P.tau;
+    if (P.beta_rho != C(0) && tau > C(0)) {
+        const C rho_hat = C(1) + dR - drho_prev;
+        tau *= Arith<C>::exp(Arith<C>::div(P.beta_rho * (rho_hat - P.rho_ref), P.rho_ref));
+    }
+    const C Dxx = C(2) * ka, Dxy = kb + kc, Dyy = C(2) * ke;
+    const C sII = Arith<C>::sqrt(C(0.5) * (Dxx * Dxx + C(2) * Dxy * Dxy + Dyy * Dyy));
+    *phi = 0.0;
+    if (P.tau_f > C(0) && tau > C(0)) {
+        const double phi_ss = 1.0 / (double)tau + (double)sII * (double)P.inv_gc;
+        const double tf = (double)P.tau_f;
+        *phi = phi_old > 0.0 ? (tf * phi_old + phi_ss) / (tf + 1.0) : phi_ss;
+        return (C)(1.0 / *phi);
+    }
+    return Arith<C>::div(tau, C(1) + tau * sII * P.inv_gc);
 }
 
 // Collision increments D_i = Delta_i + F_i = F_i + (n^eq_i - n_i)/tau_LB, with n^eq of Eq. (neq)

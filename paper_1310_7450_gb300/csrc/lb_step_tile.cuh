@@ -11,7 +11,8 @@
 //            and the BGK collision; store n*, delta rho, optional stress / velocity / residual.
 // The comparison schemes of Sec. II C run here too: the generalized-Newtonian tau_LB(gdot)
 // (scheme 1) and the divergence of Sigma^nN as a force density (scheme 2, two launches per step:
-// F_SNN writes Sigma^nN of every node, then the step with F_DIV differentiates it).
+// F_SNN writes Sigma^nN of every node, then the step with F_DIV differentiates it); scheme 3 is
+// the paper's forcing with the relaxation-time extensions (tau(rho), fluidity memory).
 // A full-width tile (nxt == nx) wraps x inside the tile and needs no x halo.
 #pragma once
 
@@ -176,6 +177,11 @@ __global__ void __launch_bounds__(NT) k_step_tile(const StepArgs<T, C> a) {
         if constexpr (SCHEME == 1) {
             s = constitutive_gn<C>(P, ka, kb, kc, ke, dR, jx, jy, &om);
             k2 = C(1) - C(0.5) * om;
+        } else if constexpr (SCHEME == 3) {
+            double phi_new;
+            const C tau_M = relaxation_time_ext<C>(P, ka, kb, kc, ke, dR, drho_prev, a.phi[P.base + pn], &phi_new);
+            s = constitutive<C, SMODE, true>(P, ka, kb, kc, ke, dR, jx, jy, drho_prev, so_xx, so_xy, so_yy, tau_M);
+            if (!(a.flags & F_FIELDS) && P.tau_f > C(0)) a.phi[P.base + pn] = phi_new;  // own node only
         } else {
             s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dR, jx, jy, drho_prev, so_xx, so_xy, so_yy);
         }

@@ -22,7 +22,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_ETIMEOUT, LB_ESTATE = ra
 LB_PREC_F64, LB_PREC_F32, LB_PREC_BF16 = 0, 1, 2
 LB_STRESS_INLM, LB_STRESS_TIMESTEPPED = 0, 1
 LB_GRID_STORE_SIGMA, LB_GRID_TILE_ONLY, LB_GRID_BF16_STOCHASTIC, LB_GRID_NO_GRAPH = 1, 2, 4, 8
-LB_GRID_GENERALIZED_NEWTONIAN, LB_GRID_STRESS_DIVERGENCE = 16, 32
+LB_GRID_GENERALIZED_NEWTONIAN, LB_GRID_STRESS_DIVERGENCE, LB_GRID_RELAXATION_MODEL = 16, 32, 64
 SCHEME_FLAGS = {"paper": 0, "generalized_newtonian": LB_GRID_GENERALIZED_NEWTONIAN,
                 "stress_divergence": LB_GRID_STRESS_DIVERGENCE}
 LB_X_PERIODIC, LB_X_GPBC = 1, 2
@@ -87,6 +87,7 @@ def load():
         "lb_channel_status": ([_H, POINTER(c_int)], c_int),
         "lb_set_wait_limit": ([_H, c_double], c_int),
         "lb_set_monitor_mode": ([_H, c_int], c_int),
+        "lb_set_relaxation_model": ([_H, c_int, c_double, c_double, c_double], c_int),
         "lb_step_count": ([_H], c_long),
         "lb_mlp_create": ([c_int, c_int, c_int, c_int, c_uint64, c_void_p, POINTER(c_void_p)], c_int),
         "lb_mlp_destroy": ([_H], None),
@@ -224,6 +225,11 @@ def lb_get_state(h: int, buf: np.ndarray):
 
 def lb_set_state(h: int, buf: np.ndarray):
     _check(load().lb_set_state(h, c_void_p(buf.ctypes.data), buf.nbytes), "lb_set_state")
+
+
+def lb_set_relaxation_model(h: int, channel: int, beta_rho: float, rho_ref: float, tau_f: float):
+    _check(load().lb_set_relaxation_model(h, int(channel), float(beta_rho), float(rho_ref), float(tau_f)),
+           "lb_set_relaxation_model")
 
 
 def lb_set_monitor_mode(h: int, mode: int):

@@ -130,3 +130,13 @@ def test_comparison_scheme_combinations_rejected_before_device_work(lib, flags, 
         lbnlm.lb_create(4, 16, p, 0, stress_mode, flags, None, x_mode, walls)
     assert e.value.status == lbnlm.LB_EINVAL
     assert "scheme" in lbnlm.lb_last_error()
+
+
+@pytest.mark.parametrize("flags,precision", [(16 | 64, 0), (32 | 64, 1), (64, 3), (64, 4)])
+def test_relaxation_model_combinations_rejected_before_device_work(lib, flags, precision):
+    """LB_GRID_RELAXATION_MODEL with a comparison scheme, or with a mixed diagnostic precision."""
+    from paper_1310_7450_gb300 import lbnlm
+    p = dict(tau_lb=0.9, g_x=1e-6, G_inf=1e-3, tau0=1.0, theta=10.0, gamma_c=0.1, rho0=1.0)
+    with pytest.raises(lbnlm.LBError) as e:
+        lbnlm.lb_create(4, 16, p, precision, 0, flags)
+    assert e.value.status == lbnlm.LB_EINVAL
