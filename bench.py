@@ -311,6 +311,13 @@ def run_gpu(args):
                             "call": "lb_set_body_force + lb_step(1) + lb_monitor (blocking) per step, LB_MONITOR_FLUX_MAX"}}
     sim.close()
 
+    # the second half of the metric: the warm-started batched sweep against the plain per-channel
+    # scheme (compact: a smaller training draw than the full --workload warmstart run)
+    sweep = None
+    if not args.no_sweep and ws == 1:
+        sweep = warm_sweep(stream.cuda_stream, "f32", args.sweep_train, 5, 512, 55, 1e-8, 1000, args.sweep_cap,
+                           args.sweep_epochs, 1e-3, plain_sample=args.sweep_plain)
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -343,7 +350,8 @@ def run_gpu(args):
                        "l2": f"state {bpn * nodes / 2**30:.2f} GiB per step, larger than the 126 MB L2 (no flush)",
                        "parallelism": f"{ws} independent replica(s)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": sampler.summary()}
+            "clocks": sampler.summary(),
+            "sweep": sweep if sweep is not None else {"skipped": "--no-sweep or more than one GPU"}}
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -514,120 +522,155 @@ def run_sweep(args):
     return 0
 
 
-def run_warmstart(args):
-    """Learned warm start.  Training set: `train` channels drawn like the batched sweep (seed
-    `train_seed`), relaxed to steady states by the persistent sweep (started from the closed-form
-    profile to save time -- the converged state does not depend on the start), resampled to 256
-    points; the perceptron (lb_mlp kernels) is trained on them.  Held out: `channels` draws (seed
-    `sweep_seed`), each run to steady from rest, from the closed-form profile and from the
-    surrogate's prediction; steps, wall time and the surrogate's error against the converged LB
-    profiles are reported.  "mlp_judged": per channel the better of the surrogate's and the closed-form
-    start after two check intervals of the batched sweep (the LB scheme as judge; its trial runs are
-    included in the wall time)."""
+def plain_to_steady(ny, p, precision, sid, tol, check, cap):
+    """The plain per-channel FP32 scheme from rest, run for real: one single-channel handle, lb_step in
+    chunks of `check` steps, and after each chunk the check-interval residual ||u(t) - u(t-k)|| /
+    (k ||u(t)||) of the batched sweep (the same convergence measure) from two velocity fields on the
+    device (lb_field_monitor_static).  Returns (steps to converge or -1 at the cap, wall seconds)."""
     import torch
-    from paper_1310_7450_gb300 import build as libbuild
+    from paper_1310_7450_gb300 import lbnlm
+    sim = lbnlm.Channels(4, ny, p, precision, stream=sid)
+    n = 4 * ny
+    u_prev = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    u_now = torch.zeros_like(u_prev)
+    offs = torch.tensor([0, n], dtype=torch.int64, device="cuda")
+    mon = torch.zeros(3, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, done = 0, -1
+    lbnlm.lb_get_fields(sim.h, u_prev, None, None, 0, True)
+    while steps < cap:
+        sim.step(check)
+        steps += check
+        lbnlm.lb_get_fields(sim.h, u_now, None, None, 0, True)
+        lbnlm.lb_field_monitor_static(u_now, u_prev, 0, 1, offs, 4, mon, sid)
+        if float(mon[0].item()) / check <= tol:
+            done = steps
+            break
+        u_prev, u_now = u_now, u_prev
+    wall = time.perf_counter() - t0
+    sim.close()
+    return done, wall
+
+
+def warm_sweep(sid, precision, train_n, train_seed, held_n, held_seed, tol, check, cap, epochs, lr,
+               plain_sample=0, judged=False, skip_rest=False):
+    """The learned warm start end to end, every profile step on the device: training data = steady
+    states of the batched sweep (`train_n` draws like the batched sweep, seed `train_seed`, started
+    from the closed form; targets encoded by lb_warmstart_targets); the perceptron trained by the
+    library's kernels; `held_n` held-out draws (seed `held_seed`) run to steady from the surrogate's
+    start (decoded by lb_warmstart_apply), from the closed form and from rest, all under the step cap
+    `cap`; optionally the LB-judged start, and the plain per-channel FP32 scheme from rest run to
+    convergence for real on a stratified sample of `plain_sample` held-out channels."""
+    import torch
     from paper_1310_7450_gb300 import inputs, lbnlm, warmstart
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    libbuild.build()
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    sid = stream.cuda_stream
 
     def draw(n, seed):
         ps = inputs.sweep_channel_params(n, seed)
         return [q.pop("ny") for q in ps], ps
 
-    def steady(nys, ps, start):
-        sim = lbnlm.Channels(4, nys, ps, args.precision, stream=sid)
-        if start == "analytic":
-            warmstart.apply(sim, [warmstart.analytic_rows(ny, q) for ny, q in zip(nys, ps)])
-        elif start is not None:
-            warmstart.apply(sim, start)
+    def steady(nys, ps, start, keep=False):
+        sim = lbnlm.Channels(4, nys, ps, precision, stream=sid)
+        if start is not None:
+            start(sim)
         lbnlm.lb_sweep_tune(sim.h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        steps, res = sim.run_until_steady(args.tol, check_every=args.check, max_steps=args.max_steps)
+        steps, _ = sim.run_until_steady(tol, check_every=check, max_steps=cap)
         wall = time.perf_counter() - t0
-        fl = sim.fields()
+        if keep:
+            return steps, wall, sim
         sim.close()
-        return steps, res, wall, fl
+        return steps, wall, None
 
     t_all = time.perf_counter()
-    # 1. training data from the batched solver
-    nys_t, ps_t = draw(args.train, args.train_seed)
-    st_t, _, wall_t, fl_t = steady(nys_t, ps_t, "analytic")
+    nys_t, ps_t = draw(train_n, train_seed)
+    st_t, wall_t, sim_t = steady(nys_t, ps_t, warmstart.start_closed_form, keep=True)
     ok = st_t > 0
-    Y = warmstart.encode_targets([n for n, o in zip(nys_t, ok) if o], [q for q, o in zip(ps_t, ok) if o],
-                                 [f[0][:, 0, 0] for f, o in zip(fl_t, ok) if o],
-                                 [f[1][:, 0, 3] for f, o in zip(fl_t, ok) if o],
-                                 [f[1][:, 0, 0] - f[1][:, 0, 1] for f, o in zip(fl_t, ok) if o])
+    Y = warmstart.steady_targets(sim_t)[torch.tensor(np.flatnonzero(ok), device="cuda")]
+    sim_t.close()
     X = warmstart.features([n for n, o in zip(nys_t, ok) if o], [q for q, o in zip(ps_t, ok) if o])
-    # 2. training with the library's kernels
     sur = warmstart.Surrogate(width=256, max_batch=512, seed=1, stream=sid)
     t0 = time.perf_counter()
-    losses = sur.fit(X, Y, epochs=args.epochs, batch=256, lr=args.lr)
+    losses = sur.fit(X, Y, epochs=epochs, batch=256, lr=lr)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    # 3. held-out channels
-    nys, ps = draw(args.channels, args.sweep_seed)
-    t0 = time.perf_counter()
-    pred = warmstart.decode(nys, ps, sur.predict(warmstart.features(nys, ps)))
-    rows = [tuple(warmstart.to_rows(f, ny) for f in prof) for ny, prof in zip(nys, pred)]
-    infer_s = time.perf_counter() - t0
-    cf_rows = [warmstart.analytic_rows(ny, q) for ny, q in zip(nys, ps)]
-    # the LB scheme as judge: two check intervals from each start, the better one per channel
-    t0 = time.perf_counter()
-    judged, pick = warmstart.judge(4, nys, ps, [rows, cf_rows], args.precision, sid, check=args.check)
-    torch.cuda.synchronize()
-    judge_s = time.perf_counter() - t0
-    res = {}
-    for name, start in (("mlp", rows), ("mlp_judged", judged), ("analytic", "analytic"), ("rest", None)):
-        if name == "rest" and args.skip_cold:
-            continue
-        st, r, wall, fl = steady(nys, ps, start)
-        if name == "mlp_judged":
-            wall += judge_s
+    nys, ps = draw(held_n, held_seed)
+    mlp_start = lambda sim: sur.start(sim, nys, ps)
+
+    def start_u(start):  # the velocity field a start writes, before any step
+        sim = lbnlm.Channels(4, nys, ps, precision, stream=sid)
+        start(sim)
+        fl = [f[0][:, 0, 0] for f in sim.fields()]
+        sim.close()
+        return fl
+    arms = [("mlp", mlp_start), ("closed_form", warmstart.start_closed_form)]
+    judge_s, pick = None, None
+    if judged:
+        t0 = time.perf_counter()
+        pick = warmstart.judge(4, nys, ps, [mlp_start, warmstart.start_closed_form], precision, sid, check=check)
+        torch.cuda.synchronize()
+        judge_s = time.perf_counter() - t0
+    if not skip_rest:
+        arms.append(("rest", None))
+    res, conv_u = {}, None
+    for name, start in arms:
+        st, wall, sim = steady(nys, ps, start, keep=(name == "closed_form"))
+        res[name] = {"wall_s": wall, "converged": int((st > 0).sum()), "steps_sum": int(np.where(st > 0, st, cap).sum()),
+                     "steps_max": int(st.max()) if (st > 0).all() else cap,
+                     "steps_median": float(np.median(np.where(st > 0, st, cap)))}
         if name == "rest":
             st_rest = st
-        res[name] = {"wall_s": wall, "converged": int((st > 0).sum()), "steps_sum": int(st[st > 0].sum()),
-                     "steps_max": int(st.max()), "steps_median": float(np.median(st[st > 0])) if (st > 0).any() else None}
-        if name == "analytic":
-            fl_ref = fl
-    # error of each start against the converged LB profiles (relative infinity norm per field); the
-    # reference is the converged state of the closed-form-started run
-    def start_errors(starts):
-        errs = {"u": [], "sxy": [], "N1": []}
-        for k, prof in enumerate(starts):
-            u_lb = fl_ref[k][0][:, 0, 0]; s_lb = fl_ref[k][1][:, 0, 3]; n_lb = fl_ref[k][1][:, 0, 0] - fl_ref[k][1][:, 0, 1]
-            for key, a, b in (("u", prof[0], u_lb), ("sxy", prof[1], s_lb), ("N1", prof[2], n_lb)):
-                errs[key].append(float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)))
-        return errs
-    # the plain per-channel FP32 scheme from rest on the same channels: its per-step time on a
-    # sample, times the steps each channel took from rest in the sweep (the cap where it did not
-    # converge, so this is a lower bound)
-    plain = None
-    if "rest" in res:
-        per_step, fit = plain_per_step(nys, ps, args, stream)
-        cap = int(args.max_steps)
-        est = float(sum((st_rest[c] if st_rest[c] > 0 else cap) * np.polyval(fit, nys[c]) for c in range(len(nys))))
-        plain = {"estimated_s_lower_bound": est, "per_step_us_by_ny": {str(nys[c]): round(1e6 * v, 2) for c, v in per_step.items()},
-                 "converged_within_cap": int((st_rest > 0).sum())}
-    err_mlp = start_errors(rows)
-    err_cf = start_errors(cf_rows)
+        if sim is not None:
+            conv_u = [f[0][:, 0, 0] for f in sim.fields()]
+            sim.close()
+    errs = {}
+    for name, start in (("mlp", mlp_start), ("closed_form", warmstart.start_closed_form)):
+        e = [float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)) for a, b in zip(start_u(start), conv_u)]
+        errs[name] = {"median": float(np.median(e)), "p90": float(np.percentile(e, 90))}
     sur.close()
+    plain = None
+    if plain_sample > 0:
+        order = np.argsort(nys)
+        sample = order[np.linspace(0, len(order) - 1, plain_sample).astype(int)]
+        runs = []
+        for c in sample:
+            done, wall = plain_to_steady(nys[c], ps[c], precision, sid, tol, check, cap)
+            runs.append({"ny": int(nys[c]), "steps": int(done), "wall_s": wall})
+        tot = sum(r["wall_s"] for r in runs)
+        plain = {"sample": runs, "sample_wall_s": tot, "sample_converged": int(sum(r["steps"] > 0 for r in runs)),
+                 "scaled_to_all_s": tot / len(runs) * len(nys),
+                 "how": f"the plain per-channel FP32 scheme from rest, run for real to the same check-interval residual "
+                        f"and cap on {len(runs)} held-out channels stratified by width (one handle per channel, lb_step "
+                        f"chunks of {check}); scaled_to_all_s = their mean wall time x {len(nys)} channels"}
+        if "rest" in res:
+            plain["sweep_steps_of_sample_from_rest"] = [int(st_rest[c]) for c in sample]
+    return {"train_channels": train_n, "train_converged": int(ok.sum()), "train_data_sweep_s": wall_t, "train_s": train_s,
+            "epochs": epochs, "final_loss": losses[-1], "held_out": held_n, "held_seed": held_seed, "tol": tol,
+            "check_every": check, "cap": cap, "arms": res, "start_error_u_vs_converged": errs,
+            "judged": None if pick is None else {"judge_s": judge_s, "picked_mlp": int((pick == 0).sum())},
+            "plain_per_channel_from_rest": plain, "total_s": time.perf_counter() - t_all}
+
+
+def run_warmstart(args):
+    """Learned warm start at full size: `train` draws for the training data (seed `train_seed`),
+    `channels` held-out draws (seed `sweep_seed`), the LB-judged start, the plain per-channel arm on a
+    sample (`baseline_sample` channels)."""
+    import torch
+    from paper_1310_7450_gb300 import build as libbuild
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    libbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    r = warm_sweep(stream.cuda_stream, args.precision, args.train, args.train_seed, args.channels, args.sweep_seed,
+                   args.tol, args.check, args.max_steps, args.epochs, args.lr, plain_sample=args.baseline_sample,
+                   judged=True, skip_rest=args.skip_cold)
     line = {"metric": "batched-sweep time-to-steady, plain vs warm-start", "unit": "s", "higher_is_better": False,
-            "value": res["mlp"]["wall_s"], "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
-            "config": {"train_channels": args.train, "train_converged": int(ok.sum()), "held_out": args.channels,
-                       "tol": args.tol, "check_every": args.check, "epochs": args.epochs},
-            "train_data_sweep_s": wall_t, "train_s": train_s, "final_loss": losses[-1], "inference_s": infer_s,
-            "judge_s": judge_s, "judge_picked_mlp": int((pick == 0).sum()),
-            "held_out": res, "plain_per_channel_from_rest": plain,
-            "start_error_median": {"mlp": {k: float(np.median(v)) for k, v in err_mlp.items()},
-                                   "closed_form": {k: float(np.median(v)) for k, v in err_cf.items()}},
-            "start_error_p90": {"mlp": {k: float(np.percentile(v, 90)) for k, v in err_mlp.items()},
-                                "closed_form": {k: float(np.percentile(v, 90)) for k, v in err_cf.items()}},
-            "total_s": time.perf_counter() - t_all}
+            "value": r["arms"]["mlp"]["wall_s"], "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"learned warm start: {args.train} training draws, {args.channels} held out, Nx=4, "
+                                   f"Ny~U{{32..1024}}", "tol": args.tol, "check_every": args.check, "cap": args.max_steps},
+            "warm_start": r}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -649,6 +692,11 @@ def main():
     ap.add_argument("--u-wall", type=float, default=0.01)
     ap.add_argument("--tile-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-train", type=int, default=2000)
+    ap.add_argument("--sweep-cap", type=int, default=2_000_000)
+    ap.add_argument("--sweep-epochs", type=int, default=200)
+    ap.add_argument("--sweep-plain", type=int, default=6)
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-crop", type=int, default=512)

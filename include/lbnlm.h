@@ -281,6 +281,22 @@ lb_status lb_sweep_set_config(lb_handle *h, int variant, int threads, int cluste
 lb_status lb_field_monitor_static(const void *u_now, const void *u_prev, int dtype, int n_channels,
                                   const long long *node_offsets, int nx, double *out, void *cuda_stream);
 
+/* Warm starts on the device (not in the paper; the learned warm start below).  Grid: the network
+ * sees each channel on 256 points d_k = (k + 1/2)/128 - 1 across the channel (d = (y - y_c)/H);
+ * its 768 outputs per channel are, for u_x, sigma_xy and N1 in turn, (steady profile - closed form)
+ * / scale on the grid, where the closed form is the steady channel solution of Sec. III B (the
+ * quadratic for dv/dd integrated to v(1) = 0; u = (H/tau0) v) at the channel's current parameters
+ * and scale = max |closed form| per field.  Rows <-> grid by linear interpolation, end values held.
+ * lb_warmstart_apply: writes a start state into every channel from pred (device, [n_channels][768]
+ * FP32 network outputs, de-standardised as pred * t_sd + t_mu when t_mu and t_sd, device [768],
+ * are given; both or neither) or, with pred = NULL, from the closed form itself: u = (u_x(y), 0),
+ * rho = 1, delta rho = -(3/2) N1(y), as lb_set_fields does.  lb_warmstart_targets: the network
+ * targets of the handle's current state (column x = 0 of each row) into targets (device,
+ * [n_channels][768], FP32).  Both need G_inf > 0, tau0 > 0 and g_x > 0 in every channel
+ * (LB_EINVAL); both run on the handle's stream (apply synchronises it). */
+lb_status lb_warmstart_apply(lb_handle *h, const float *pred, const float *t_mu, const float *t_sd);
+lb_status lb_warmstart_targets(lb_handle *h, float *targets);
+
 /* ---- Learned warm start (not in the paper): a three-layer perceptron n_in -> width -> width ->
  * n_out (tanh hidden layers) with BF16 working weights, FP32 master weights and FP32 accumulation,
  * trained with Adam on a mean-squared-error loss by this library's kernels.  Parameters are flat

@@ -26,6 +26,18 @@
 #include "lbnlm.h"
 
 namespace lbk {
+// learned warm start (lb_warmstart.cu)
+struct WsChan {
+    double g, G, tau0, theta, gamma_c;
+};
+cudaError_t launch_ws_closed_form(int n_ch, const WsChan* prm, const int* nys, const int* row_off, double* rows,
+                                  double* grid, double* scale, cudaStream_t s);
+cudaError_t launch_ws_decode(int n_ch, const float* pred, const float* t_mu, const float* t_sd, const double* grid,
+                             const double* scale, const double* rows, const int* nys, const int* row_off,
+                             const long long* node_off, int nx, double* u, double* rho, double* drho, cudaStream_t s);
+template <typename F>
+cudaError_t launch_ws_targets(int n_ch, const F* fu, const F* fs, const double* grid, const double* scale, const int* nys,
+                              const long long* node_off, int nx, float* targets, cudaStream_t s);
 extern template cudaError_t launch_step_tile<double, double, 0>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<double, double, 1>(const StepArgs<double, double>&, int, size_t, cudaStream_t);
 extern template cudaError_t launch_step_tile<float, float, 0>(const StepArgs<float, float>&, int, size_t, cudaStream_t);
@@ -354,6 +366,9 @@ struct lb_handle {
     int scheme = 0;       // 0: the paper's forcing; 1: generalized Newtonian; 2: div Sigma^nN force;
                           // 3: the paper's forcing with the relaxation-time extensions
     std::vector<double> beta_rho, rho_ref, tau_f;  // scheme 3, per channel
+    // learned warm start: per-channel closed-form parameters, row offsets, closed form on the rows
+    // [row][3] and on the network grid [channel][3][256], scales [channel][3]
+    void *ws_prm = nullptr, *ws_row_off = nullptr, *ws_rows = nullptr, *ws_grid = nullptr, *ws_scale = nullptr;
     void* chan = nullptr;
     WorkItem* items_d = nullptr;
     int* item_begin_d = nullptr;
@@ -662,6 +677,7 @@ void release(lb_handle* h) {
     free_dev(h->partials); free_dev(h->mon_d); free_dev(h->status_d); free_dev(h->base_d); free_dev(h->P_d);
     free_dev(h->node_off_d); free_dev(h->ny_d); free_dev(h->gx_d); free_dev(h->fields); free_dev(h->fconv);
     free_dev(h->hstage);
+    free_dev(h->ws_prm); free_dev(h->ws_row_off); free_dev(h->ws_rows); free_dev(h->ws_grid); free_dev(h->ws_scale);
     free_dev(h->march_items_d);
     free_dev(h->march_item_begin_d);
     free_dev(h->sweep_steps_d);
@@ -1637,6 +1653,26 @@ lb_status lb_set_wall_velocity(lb_handle* h, int channel, double u_wall) {
     return push_drive(h);
 }
 
+// The start state of every channel from device fields in node order (u [node][2], rho, drho or
+// nullptr): equilibrium populations of (rho, u - f/(2 rho)), delta rho, zero carried stress.
+static lb_status set_fields_dev(lb_handle* h, const double* su, const double* sr, const double* sd) {
+    long long maxn = 0;
+    for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
+    dim3 g(grid_for(maxn), h->n_ch);
+    with_types(h->prec, [&](auto tt, auto tc) {
+        LB_TYPES(tt, tc);
+        k_set_fields<T, C><<<g, 256, 0, h->stream>>>((T*)h->popA, (C*)h->drho, (C*)h->sig3, su, sr, sd,
+                                                     h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode,
+                                                     h->gpbc ? 1 : 0);
+        return 0;
+    });
+    LB_CK(cudaGetLastError());
+    if (h->phi) LB_CK(cudaMemsetAsync(h->phi, 0, h->planes * sizeof(double), h->stream));  // fluidity unset
+    LB_CK(cudaStreamSynchronize(h->stream));
+    h->uprev_state = -10;
+    return LB_OK;
+}
+
 lb_status lb_set_fields(lb_handle* h, const double* u, const double* rho, const double* drho) {
     if (!h || !u || !rho) return fail(LB_EINVAL, "lb_set_fields: null argument%s");
     const long long N = h->nodes;
@@ -1648,19 +1684,66 @@ lb_status lb_set_fields(lb_handle* h, const double* u, const double* rho, const 
     LB_CK(cudaMemcpyAsync(su, u, 2 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     LB_CK(cudaMemcpyAsync(sr, rho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (drho) LB_CK(cudaMemcpyAsync(sd, drho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    long long maxn = 0;
-    for (int c = 0; c < h->n_ch; ++c) maxn = std::max(maxn, (long long)h->nx * h->ny[c]);
-    dim3 g(grid_for(maxn), h->n_ch);
-    with_types(h->prec, [&](auto tt, auto tc) {
-        LB_TYPES(tt, tc);
-        k_set_fields<T, C><<<g, 256, 0, h->stream>>>((T*)h->popA, (C*)h->drho, (C*)h->sig3, su, sr, drho ? sd : nullptr,
-                                                     h->base_d, h->P_d, h->node_off_d, h->ny_d, h->gx_d, h->nx, h->smode,
-                                                     h->gpbc ? 1 : 0);
-        return 0;
-    });
-    LB_CK(cudaGetLastError());
+    return set_fields_dev(h, su, sr, drho ? sd : nullptr);
+}
+
+// Learned warm start: the closed-form steady profile of every channel (current parameters) on its
+// rows and on the network grid, with the per-field scales.
+static lb_status ws_closed_form(lb_handle* h) {
+    if (!h->ws_prm) {
+        LB_CK(cudaMalloc(&h->ws_prm, sizeof(WsChan) * h->n_ch));
+        LB_CK(cudaMalloc(&h->ws_row_off, sizeof(int) * h->n_ch));
+        LB_CK(cudaMalloc(&h->ws_rows, sizeof(double) * 3 * (size_t)h->gny));
+        LB_CK(cudaMalloc(&h->ws_grid, sizeof(double) * 3 * 256 * (size_t)h->n_ch));
+        LB_CK(cudaMalloc(&h->ws_scale, sizeof(double) * 3 * (size_t)h->n_ch));
+        LB_CK(cudaMemcpy(h->ws_row_off, h->row_off.data(), sizeof(int) * h->n_ch, cudaMemcpyHostToDevice));
+    }
+    std::vector<WsChan> prm(h->n_ch);
+    for (int c = 0; c < h->n_ch; ++c) {
+        const lb_params& p = h->params[c];
+        if (!(p.G_inf > 0.0) || !(p.tau0 > 0.0) || !(p.g_x > 0.0))
+            return fail(LB_EINVAL, "lb_warmstart: every channel needs G_inf > 0, tau0 > 0 and g_x > 0 (the closed form)%s");
+        prm[c] = WsChan{p.g_x, p.G_inf, p.tau0, p.theta, p.gamma_c};
+    }
     LB_CK(cudaStreamSynchronize(h->stream));
-    h->uprev_state = -10;
+    LB_CK(cudaMemcpy(h->ws_prm, prm.data(), sizeof(WsChan) * h->n_ch, cudaMemcpyHostToDevice));
+    LB_CK(launch_ws_closed_form(h->n_ch, (const WsChan*)h->ws_prm, h->ny_d, (const int*)h->ws_row_off,
+                                (double*)h->ws_rows, (double*)h->ws_grid, (double*)h->ws_scale, h->stream));
+    return LB_OK;
+}
+
+lb_status lb_warmstart_apply(lb_handle* h, const float* pred, const float* t_mu, const float* t_sd) {
+    if (!h || (!t_mu) != (!t_sd)) return fail(LB_EINVAL, "lb_warmstart_apply: null handle, or only one of t_mu, t_sd%s");
+    const long long N = h->nodes;
+    lb_status st = ensure_hstage(h, (size_t)N * 4 * sizeof(double));
+    if (st != LB_OK) return st;
+    st = ws_closed_form(h);
+    if (st != LB_OK) return st;
+    double* su = (double*)h->hstage;
+    LB_CK(launch_ws_decode(h->n_ch, pred, t_mu, t_sd, (const double*)h->ws_grid, (const double*)h->ws_scale,
+                           (const double*)h->ws_rows, h->ny_d, (const int*)h->ws_row_off, h->node_off_d, h->nx, su,
+                           su + 2 * N, su + 3 * N, h->stream));
+    return set_fields_dev(h, su, su + 2 * N, su + 3 * N);
+}
+
+lb_status lb_warmstart_targets(lb_handle* h, float* targets) {
+    if (!h || !targets) return fail(LB_EINVAL, "lb_warmstart_targets: null argument%s");
+    lb_status st = ws_closed_form(h);
+    if (st != LB_OK) return st;
+    const long long N = h->nodes;
+    if (!h->fields) LB_CK(cudaMalloc(&h->fields, 7 * N * h->csize));
+    char* base = (char*)h->fields;
+    void* fu = base;
+    void* fs = base + 2 * N * h->csize;
+    void* fr = base + 6 * N * h->csize;
+    st = with_types(h->prec, [&](auto tt, auto tc) { LB_TYPES(tt, tc); return fields_pass<T, C>(h, (C*)fu, (C*)fs, (C*)fr); });
+    if (st != LB_OK) return st;
+    if (h->csize == 8)
+        LB_CK(launch_ws_targets<double>(h->n_ch, (const double*)fu, (const double*)fs, (const double*)h->ws_grid,
+                                        (const double*)h->ws_scale, h->ny_d, h->node_off_d, h->nx, targets, h->stream));
+    else
+        LB_CK(launch_ws_targets<float>(h->n_ch, (const float*)fu, (const float*)fs, (const double*)h->ws_grid,
+                                       (const double*)h->ws_scale, h->ny_d, h->node_off_d, h->nx, targets, h->stream));
     return LB_OK;
 }
 

@@ -88,6 +88,8 @@ def load():
         "lb_set_wait_limit": ([_H, c_double], c_int),
         "lb_set_monitor_mode": ([_H, c_int], c_int),
         "lb_set_relaxation_model": ([_H, c_int, c_double, c_double, c_double], c_int),
+        "lb_warmstart_apply": ([_H, c_void_p, c_void_p, c_void_p], c_int),
+        "lb_warmstart_targets": ([_H, c_void_p], c_int),
         "lb_step_count": ([_H], c_long),
         "lb_mlp_create": ([c_int, c_int, c_int, c_int, c_uint64, c_void_p, POINTER(c_void_p)], c_int),
         "lb_mlp_destroy": ([_H], None),
@@ -225,6 +227,25 @@ def lb_get_state(h: int, buf: np.ndarray):
 
 def lb_set_state(h: int, buf: np.ndarray):
     _check(load().lb_set_state(h, c_void_p(buf.ctypes.data), buf.nbytes), "lb_set_state")
+
+
+def _dev(t):
+    """Device address of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous()
+    return c_void_p(t.data_ptr())
+
+
+def lb_warmstart_apply(h: int, pred=None, t_mu=None, t_sd=None):
+    """pred: CUDA float32 [n_channels, 768] network outputs (or None: the closed form); t_mu, t_sd:
+    CUDA float32 [768] de-standardisation (both or neither)."""
+    _check(load().lb_warmstart_apply(h, _dev(pred), _dev(t_mu), _dev(t_sd)), "lb_warmstart_apply")
+
+
+def lb_warmstart_targets(h: int, targets):
+    """targets: CUDA float32 [n_channels, 768], filled on the handle's stream."""
+    _check(load().lb_warmstart_targets(h, _dev(targets)), "lb_warmstart_targets")
 
 
 def lb_set_relaxation_model(h: int, channel: int, beta_rho: float, rho_ref: float, tau_f: float):

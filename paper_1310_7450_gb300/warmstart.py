@@ -2,10 +2,12 @@
 
 The surrogate is the library's perceptron (``lbnlm.lb_mlp_*``; forward, backward and Adam run in its
 CUDA kernels).  It maps a channel's parameters to its steady profiles u_x, sigma_xy and N1 on 256
-points across the channel; ``apply`` writes a profile into a handle with ``lb_set_fields`` and the
-lattice-Boltzmann scheme then relaxes to its own steady state (it stays the judge of the result).
+points across the channel; the library decodes its outputs and writes the start state on the device
+(``lbnlm.lb_warmstart_apply``), and the lattice-Boltzmann scheme then relaxes to its own steady state
+(it stays the judge of the result).  Training targets come from steady LB states the same way
+(``lbnlm.lb_warmstart_targets``).
 
-Encoding (host-side marshalling only):
+Encoding (the arithmetic runs in the library's kernels; this module marshals):
   features  log10 Ny, log10 g, log10 G_inf, log10 theta, standardised with the training statistics;
   targets   the steady LB profiles minus the closed-form steady profile (the discretisation error
             of the lattice, which the network learns), each divided by the maximum |value| of the
@@ -18,19 +20,10 @@ import math
 
 import numpy as np
 
-from . import inputs, lbnlm
+from . import lbnlm
 
 NPTS = 256
-D_GRID = (np.arange(NPTS) + 0.5) / NPTS * 2.0 - 1.0
-
-
-def scales(ny: int, p: dict):
-    H = ny / 2.0
-    nu = inputs.nu_lb(p["tau_lb"], p.get("rho0", 1.0))
-    us = p["g_x"] * H * H / (2.0 * nu)
-    ss = p["g_x"] * H
-    ns = ss * ss / p["G_inf"]
-    return us, ss, ns
+N_OUT = 3 * NPTS
 
 
 def features(nys, params) -> np.ndarray:
@@ -38,51 +31,25 @@ def features(nys, params) -> np.ndarray:
                      for ny, p in zip(nys, params)], dtype=np.float64)
 
 
-def rows_d(ny: int) -> np.ndarray:
-    return (np.arange(ny) - (ny - 1) / 2.0) / (ny / 2.0)
+def steady_targets(sim):
+    """Network targets of the current (steady) state of every channel of ``sim`` (an
+    lbnlm.Channels): a CUDA float32 tensor [n_channels, 768]."""
+    import torch
+    y = torch.empty((len(sim.ny), N_OUT), dtype=torch.float32, device="cuda")
+    lbnlm.lb_warmstart_targets(sim.h, y)
+    return y
 
 
-def to_grid(profile_rows: np.ndarray, ny: int) -> np.ndarray:
-    """Linear interpolation of a profile on the ny rows onto the 256-point grid (end values held)."""
-    return np.interp(D_GRID, rows_d(ny), profile_rows)
-
-
-def to_rows(profile_grid: np.ndarray, ny: int) -> np.ndarray:
-    return np.interp(rows_d(ny), D_GRID, profile_grid)
-
-
-def closed_form_grid(ny: int, p: dict):
-    """Closed-form (u, sxy, N1) of the channel on the 256-point grid and the per-field scales."""
-    prof = [to_grid(f, ny) for f in analytic_rows(ny, p)]
-    sc = [max(np.abs(f).max(), 1e-300) for f in prof]
-    return prof, sc
-
-
-def encode_targets(nys, params, u_rows, sxy_rows, n1_rows) -> np.ndarray:
-    """Per channel: [(LB - closed form)/scale for u, sxy, N1 on the 256 points]."""
-    out = np.zeros((len(nys), 3 * NPTS))
-    for k, (ny, p) in enumerate(zip(nys, params)):
-        ref, sc = closed_form_grid(ny, p)
-        lb = [to_grid(u_rows[k], ny), to_grid(sxy_rows[k], ny), to_grid(n1_rows[k], ny)]
-        for j in range(3):
-            out[k, j * NPTS:(j + 1) * NPTS] = (lb[j] - ref[j]) / sc[j]
-    return out
-
-
-def decode(nys, params, pred: np.ndarray):
-    """Inverse of encode_targets on the 256-point grid: lists of (u, sxy, N1) arrays per channel."""
-    res = []
-    for k, (ny, p) in enumerate(zip(nys, params)):
-        ref, sc = closed_form_grid(ny, p)
-        res.append(tuple(ref[j] + sc[j] * pred[k, j * NPTS:(j + 1) * NPTS] for j in range(3)))
-    return res
+def start_closed_form(sim):
+    """Start every channel of ``sim`` from the closed-form steady profile (on the device)."""
+    lbnlm.lb_warmstart_apply(sim.h)
 
 
 class Surrogate:
     """Feature / target standardisation around an lb_mlp handle."""
 
     def __init__(self, width=256, max_batch=512, seed=0, stream=None):
-        self.n_in, self.n_out, self.width = 4, 3 * NPTS, width
+        self.n_in, self.n_out, self.width = 4, N_OUT, width
         self.m = lbnlm.lb_mlp_create(self.n_in, width, self.n_out, max_batch, seed, stream)
         self.max_batch = max_batch
         self.fmu = self.fsd = self.tmu = self.tsd = None
@@ -93,11 +60,15 @@ class Surrogate:
             self.m = None
 
     def fit(self, X, Y, epochs=200, batch=256, lr=1e-3, seed=0, log=None):
+        """X: host features [n, 4]; Y: targets [n, 768], a CUDA tensor (steady_targets) or host array."""
         import torch
         self.fmu, self.fsd = X.mean(0), X.std(0) + 1e-12
-        self.tmu, self.tsd = Y.mean(0), Y.std(0) + 1e-6
+        ys = Y if isinstance(Y, torch.Tensor) else torch.tensor(Y, dtype=torch.float32, device="cuda")
+        ys = ys.to(device="cuda", dtype=torch.float32)
+        self.tmu = ys.mean(0).contiguous()
+        self.tsd = (ys.std(0) + 1e-6).contiguous()
+        ys = ((ys - self.tmu) / self.tsd).contiguous()
         xs = torch.tensor((X - self.fmu) / self.fsd, dtype=torch.float32, device="cuda")
-        ys = torch.tensor((Y - self.tmu) / self.tsd, dtype=torch.float32, device="cuda")
         n = xs.shape[0]
         rng = np.random.default_rng(seed)
         losses = []
@@ -118,71 +89,47 @@ class Surrogate:
                 log(f"epoch {ep} loss {losses[-1]:.3e}")
         return losses
 
-    def predict(self, X) -> np.ndarray:
+    def predict_device(self, X):
+        """Standardised network outputs for host features X [n, 4]: a CUDA float32 tensor [n, 768]."""
         import torch
-        out = np.zeros((X.shape[0], self.n_out))
+        out = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device="cuda")
         for s in range(0, X.shape[0], self.max_batch):
             xb = torch.tensor((X[s:s + self.max_batch] - self.fmu) / self.fsd, dtype=torch.float32, device="cuda")
-            yb = torch.zeros((xb.shape[0], self.n_out), dtype=torch.float32, device="cuda")
-            lbnlm.lb_mlp_forward(self.m, xb.contiguous(), xb.shape[0], yb)
-            torch.cuda.synchronize()
-            out[s:s + xb.shape[0]] = yb.cpu().numpy() * self.tsd + self.tmu
+            lbnlm.lb_mlp_forward(self.m, xb.contiguous(), xb.shape[0], out[s:s + xb.shape[0]])
         return out
 
-
-def analytic_rows(ny: int, p: dict, n: int = 4001):
-    """Closed-form steady channel (the quadratic for dv/dd of Sec. III B, integrated with the
-    trapezoid rule on n points so that v(1) = 0): u_x, sigma_xy, N1 on the rows."""
-    H = ny / 2.0
-    G, tau0, theta, gc = p["G_inf"], p["tau0"], p["theta"], p.get("gamma_c", 0.1)
-    wpH = p["g_x"] * H / G
-    d = np.linspace(0.0, 1.0, n)
-    if theta == 0.0:
-        dv = -wpH * d
-    else:
-        a = wpH * d / 2.0
-        b = gc * (1.0 + theta) / (2.0 * theta)
-        dv = -a + b - np.sqrt((a - b) ** 2 + wpH * d * gc / theta)
-    v = np.concatenate([[0.0], np.cumsum(0.5 * (dv[1:] + dv[:-1]) * np.diff(d))])
-    v = v - v[-1]
-    dd = np.abs(rows_d(ny))
-    u = (H / tau0) * np.interp(dd, d, v)
-    gdot = np.interp(dd, d, dv) / tau0 * np.sign(rows_d(ny))
-    tau = theta * tau0
-    tau_m = tau / (1.0 + tau * np.abs(gdot) / gc) if tau > 0 else np.zeros_like(gdot)
-    sxy = G * tau_m * gdot
-    n1 = 2.0 * G * gdot ** 2 * tau_m ** 2
-    return u, sxy, n1
+    def start(self, sim, nys, params):
+        """Start every channel of ``sim`` from the surrogate's prediction (decoded on the device)."""
+        pred = self.predict_device(features(nys, params))
+        lbnlm.lb_warmstart_apply(sim.h, pred, self.tmu, self.tsd)
 
 
-def judge(nx, nys, params, candidates, precision="f32", stream=None, check=1000):
-    """The lattice-Boltzmann scheme as the judge of the starts: every candidate (a list of per-channel
-    (u_x, sigma_xy, N1) row profiles) runs two check intervals of the batched sweep; per channel the
-    candidate with the smallest check-interval residual wins.  Returns (chosen rows, index of the
-    winning candidate per channel)."""
+def judge(nx, nys, params, starts, precision="f32", stream=None, check=1000):
+    """The lattice-Boltzmann scheme as the judge of the starts: every candidate start (a function
+    that writes a start state into an lbnlm.Channels) runs two check intervals of the batched sweep;
+    per channel the candidate with the smallest check-interval residual wins.  Returns the index of
+    the winning candidate per channel."""
     res = []
-    for rows in candidates:
+    for start in starts:
         sim = lbnlm.Channels(nx, nys, params, precision, stream=stream)
         try:
-            apply(sim, rows)
+            start(sim)
             _, r = sim.run_until_steady(0.0, check_every=check, max_steps=2 * check)
         finally:
             sim.close()
         res.append(np.where(np.isfinite(r), r, np.inf))
-    pick = np.argmin(np.array(res), axis=0)
-    return [candidates[k][c] for c, k in enumerate(pick)], pick
+    return np.argmin(np.array(res), axis=0)
 
 
-def apply(sim, rows_by_channel):
-    """Write (u_x, sigma_xy, N1) row profiles into every channel of ``sim`` (an lbnlm.Channels):
-    u = (u_x, 0), rho = 1 and the stored flow-induced density delta rho = -(3/2) tr sigma with
-    tr sigma = N1 in a simple-shear profile."""
+def apply_fields(sim, ux_rows_by_channel, n1_rows_by_channel):
+    """Write given row profiles (host arrays) into every channel of ``sim``: u = (u_x, 0), rho = 1,
+    delta rho = -(3/2) N1 (the trace of a simple-shear stress is N1), through lb_set_fields."""
     nx = sim.nx
     u = np.zeros((sim.nodes, 2))
     rho = np.ones(sim.nodes)
     drho = np.zeros(sim.nodes)
     o = 0
-    for ny, (ux, sxy, n1) in zip(sim.ny, rows_by_channel):
+    for ny, ux, n1 in zip(sim.ny, ux_rows_by_channel, n1_rows_by_channel):
         n = ny * nx
         u[o:o + n, 0] = np.repeat(ux, nx)
         drho[o:o + n] = np.repeat(-1.5 * n1, nx)

@@ -32,7 +32,7 @@ def test_paper_grids_steady_profile_within_one_percent():
     nys = [c[0] for c in cases]
     ps = [channel(ny, th) for ny, th in cases]
     with lbnlm.Channels(4, nys, ps, "f64", stream=stream) as sim:
-        warmstart.apply(sim, [warmstart.analytic_rows(ny, p) for ny, p in zip(nys, ps)])
+        warmstart.start_closed_form(sim)
         steps, res = sim.run_until_steady(-1.0, check_every=1000, max_steps=4_000_000)
         fl = sim.fields()
     bound = GOLDEN["velocity_error_theta_1000"]["value"]

@@ -17,6 +17,7 @@ import pytest
 
 import oracle
 from oracle import analytic
+import warmstart_reference as ref
 from paper_1310_7450_gb300 import inputs, lbnlm, warmstart
 
 pytestmark = pytest.mark.gpu
@@ -33,7 +34,7 @@ def test_reduced_precision_8192x2048():
     cfg = inputs.reduced_precision_channel()
     nx, ny, p = cfg["nx"], cfg["ny"], cfg["params"]
     steps = 100_000
-    start = warmstart.analytic_rows(ny, p)
+    start = ref.analytic_rows(ny, p)   # (the library computes the same closed form on the device)
     ua = analytic.channel_profile(ny, p["g_x"], p["G_inf"], p["tau0"], p["theta"], p["gamma_c"])
     # FP64 oracle on 4 x 2048 from the same closed-form start
     st = oracle.flow_state(np.ones((ny, 4)), np.repeat(start[0][:, None], 4, 1), np.zeros((ny, 4)), p["g_x"])
@@ -44,7 +45,7 @@ def test_reduced_precision_8192x2048():
     for name, prec, flags in (("f32", "f32", 0), ("bf16", "bf16", 0), ("bf16_sr", "bf16", lbnlm.LB_GRID_BF16_STOCHASTIC)):
         with lbnlm.Channels(nx, ny, p, prec, flags=flags | lbnlm.LB_GRID_STORE_SIGMA, stream=stream) as sim:
             assert lbnlm.lb_uses_row_march(sim.h)
-            warmstart.apply(sim, [start])
+            warmstart.start_closed_form(sim)
             sim.step(steps)
             (u, s, _), = sim.fields()
         if flags & lbnlm.LB_GRID_BF16_STOCHASTIC:

@@ -1,9 +1,11 @@
-"""Host-side pieces of the warm start: the closed-form initial profile (an independent trapezoid
-evaluation of the steady channel solution) against the oracle's adaptive quadrature, and the
-target encoding round trip."""
+"""The NumPy reference of the warm start's profile arithmetic (the library runs it on the device;
+tests/warmstart_reference.py): its closed-form initial profile (a trapezoid evaluation of the steady
+channel solution) against the oracle's adaptive quadrature, and the target encoding round trip;
+the network features."""
 import numpy as np
 import pytest
 
+import warmstart_reference as ref
 from oracle import analytic
 from paper_1310_7450_gb300 import inputs, warmstart
 
@@ -13,7 +15,7 @@ def test_closed_form_start_matches_oracle_quadrature(theta, wpH):
     ny = 64
     G = 1e-4
     p = inputs.matched_params(0.9, theta, 0.1, G, wpH * G / (ny / 2))
-    u, sxy, n1 = warmstart.analytic_rows(ny, p)
+    u, sxy, n1 = ref.analytic_rows(ny, p)
     ua = analytic.channel_profile(ny, p["g_x"], G, p["tau0"], theta, 0.1)
     assert np.abs(u - ua).max() <= 2e-4 * np.abs(ua).max()
     gd = analytic.channel_shear_rate(ny, p["g_x"], G, p["tau0"], theta, 0.1)
@@ -30,15 +32,15 @@ def test_encode_decode_roundtrip():
     us = [rng.uniform(0, 1, n) for n in nys]
     ss = [rng.uniform(-1, 1, n) for n in nys]
     ns = [rng.uniform(0, 1, n) for n in nys]
-    Y = warmstart.encode_targets(nys, ps, us, ss, ns)
-    assert Y.shape == (3, 3 * warmstart.NPTS)
-    back = warmstart.decode(nys, ps, Y)
+    Y = ref.encode_targets(nys, ps, us, ss, ns)
+    assert Y.shape == (3, 3 * warmstart.NPTS) and ref.NPTS == warmstart.NPTS
+    back = ref.decode(nys, ps, Y)
     for k, ny in enumerate(nys):
         for j, src in enumerate((us, ss, ns)):
-            np.testing.assert_allclose(back[k][j], warmstart.to_grid(src[k], ny), rtol=1e-10, atol=1e-12 * np.abs(src[k]).max())
+            np.testing.assert_allclose(back[k][j], ref.to_grid(src[k], ny), rtol=1e-10, atol=1e-12 * np.abs(src[k]).max())
     # a zero prediction is the closed-form start
-    zero = warmstart.decode(nys, ps, np.zeros_like(Y))
+    zero = ref.decode(nys, ps, np.zeros_like(Y))
     for k, ny in enumerate(nys):
-        np.testing.assert_allclose(zero[k][0], warmstart.to_grid(warmstart.analytic_rows(ny, ps[k])[0], ny), rtol=1e-12)
+        np.testing.assert_allclose(zero[k][0], ref.to_grid(ref.analytic_rows(ny, ps[k])[0], ny), rtol=1e-12)
     X = warmstart.features(nys, ps)
     assert X.shape == (3, 4) and np.all(np.isfinite(X))
