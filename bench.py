@@ -645,7 +645,9 @@ def warm_sweep(sid, precision, train_n, train_seed, held_n, held_seed, tol, chec
                         f"chunks of {check}); scaled_to_all_s = their mean wall time x {len(nys)} channels"}
         if "rest" in res:
             plain["sweep_steps_of_sample_from_rest"] = [int(st_rest[c]) for c in sample]
+    train_tflops = sur.flops_per_step(sur.batch_used) * sur.steps_done / train_s / 1e12 if train_s > 0 else None
     return {"train_channels": train_n, "train_converged": int(ok.sum()), "train_data_sweep_s": wall_t, "train_s": train_s,
+            "train_tflops": train_tflops, "train_steps": sur.steps_done,
             "epochs": epochs, "final_loss": losses[-1], "held_out": held_n, "held_seed": held_seed, "tol": tol,
             "check_every": check, "cap": cap, "arms": res, "start_error_u_vs_converged": errs,
             "judged": None if pick is None else {"judge_s": judge_s, "picked_mlp": int((pick == 0).sum())},

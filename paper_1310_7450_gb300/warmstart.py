@@ -60,7 +60,8 @@ class Surrogate:
             self.m = None
 
     def fit(self, X, Y, epochs=200, batch=256, lr=1e-3, seed=0, log=None):
-        """X: host features [n, 4]; Y: targets [n, 768], a CUDA tensor (steady_targets) or host array."""
+        """X: host features [n, 4]; Y: targets [n, 768], a CUDA tensor (steady_targets) or host array.
+        Returns the loss of each epoch's last batch."""
         import torch
         self.fmu, self.fsd = X.mean(0), X.std(0) + 1e-12
         ys = Y if isinstance(Y, torch.Tensor) else torch.tensor(Y, dtype=torch.float32, device="cuda")
@@ -73,21 +74,29 @@ class Surrogate:
         rng = np.random.default_rng(seed)
         losses = []
         batch = min(batch, self.max_batch, n)
+        self.steps_done, self.batch_used = 0, batch
         for ep in range(epochs):
             perm = torch.tensor(rng.permutation(n), device="cuda")
             rate = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))  # cosine schedule
-            tot = 0.0
-            nb = 0
-            for s in range(0, n - batch + 1, batch):
+            starts = range(0, n - batch + 1, batch)
+            last = None
+            for s in starts:
                 idx = perm[s:s + batch]
                 xb = xs.index_select(0, idx).contiguous()
                 yb = ys.index_select(0, idx).contiguous()
-                tot += lbnlm.lb_mlp_train_step(self.m, xb, yb, batch, max(rate, 1e-6))
-                nb += 1
-            losses.append(tot / max(nb, 1))
+                # the loss comes back (and the stream is waited for) on the epoch's last batch only
+                last = lbnlm.lb_mlp_train_step(self.m, xb, yb, batch, max(rate, 1e-6), want_loss=(s == starts[-1]))
+                self.steps_done += 1
+            losses.append(last)
             if log and (ep % 50 == 0 or ep == epochs - 1):
                 log(f"epoch {ep} loss {losses[-1]:.3e}")
         return losses
+
+    def flops_per_step(self, batch):
+        """Multiply-add FLOPs of one training step (forward, the three weight gradients and the two
+        input gradients of the hidden layers)."""
+        i, h, o = self.n_in, self.width, self.n_out
+        return 2 * batch * ((i * h + h * h + h * o) + (i * h + h * h + h * o) + (h * h + h * o))
 
     def predict_device(self, X):
         """Standardised network outputs for host features X [n, 4]: a CUDA float32 tensor [n, 768]."""
