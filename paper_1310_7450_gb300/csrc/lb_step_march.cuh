@@ -600,9 +600,10 @@ constexpr int kMarchK = 8;    // shared-memory row slots (copies run K-2 rows ah
 // work and pack their stores into bf16x2 words (497 -> 366 instructions per node; with 7 CTAs per
 // SM 57.7 -> 73.8 GLUPS at 4096 x 4096).  The FP32 step is
 // bound by HBM and keeps one column per thread (two measured 4 % slower: a 64-thread CTA at 161
-// registers leaves 10 warps per SM to cover the memory latency).  The boundary variants keep one.
+// registers leaves 10 warps per SM to cover the memory latency).  The BF16 boundary variants
+// take two columns as well (pressure-driven ends 49.8 -> 59.3, moving wall 55.1 -> 72.0 GLUPS).
 template <typename T, int BND>
-constexpr int march_nc() { return (BND == 0 && std::is_same<T, __nv_bfloat16>::value) ? LBK_MARCH_NC_BF16 : 1; }
+constexpr int march_nc() { return std::is_same<T, __nv_bfloat16>::value ? LBK_MARCH_NC_BF16 : 1; }
 
 template <typename T, typename C, int SMODE, int BND = 0>
 cudaError_t launch_step_march(const CUtensorMap& map, const StepArgs<T, C>& a, const MarchCtl& ctl, int grid,
