@@ -335,6 +335,18 @@ lb_status lb_set_wait_limit(lb_handle *h, double seconds);
 
 long lb_step_count(const lb_handle *h);     /* steps taken since creation (or restored)      */
 int lb_uses_row_march(const lb_handle *h);  /* 1 if plain steps run on the row-march kernel   */
+
+/* Work items of the row-march kernel for a single nx x ny channel (host only, no GPU needed):
+ * strips of 128 columns cut into row ranges, at most one per resident CTA (ctas_per_sm x n_sm),
+ * with rows dealt so that every item is expected to take the same time (later CTAs on an SM run
+ * slower under the warp schedulers' age priority; the two edge strips cost more per row).
+ * precision LB_PREC_F32 or LB_PREC_BF16, gpbc nonzero for pressure-driven ends (the model's edge
+ * cost depends on both).  Writes (x0, y0, y1) per item into items[3 * max_items] (caller-owned
+ * host memory; items may be NULL to query the count) and returns the number of items, or
+ * -LB_EINVAL for nx not a positive multiple of 128, ny < 16, counts < 1, another precision, or
+ * more items than max_items.  Not in the paper: a scheduling detail of this library's kernel. */
+int lb_row_march_plan(int nx, int ny, int ctas_per_sm, int n_sm, int precision, int gpbc, int *items,
+                      int max_items);
 long lb_graph_replays(const lb_handle *h);  /* CUDA-graph launches made by lb_step so far      */
 size_t lb_num_nodes(const lb_handle *h);     /* total fluid nodes over all channels           */
 void lb_destroy(lb_handle *h);               /* synchronises the stream, frees everything     */

@@ -566,6 +566,95 @@ bool make_pop_map(const lb_handle* h, void* base, CUtensorMap* map) {
     return r == CUDA_SUCCESS;
 }
 
+// Row-march work items: strips of kMarchW columns cut into row ranges, at most one item per
+// resident CTA (one wave: a partial second wave would double the kernel time for a few CTAs).
+// Items are not equally long, because CTAs are not equally fast: the warp schedulers favour older
+// warps, so the CTAs that arrive later on an SM take longer for the same rows (measured at
+// 4096 x 4096 with equal items, per CTA rank on its SM: FP32 five ranks 246 ... 275 us; BF16
+// eight ranks 182 ... 219 us; only the BF16 step gains from dealing rows by rank, see the
+// constants below), and an edge strip costs more per row than an interior one (its
+// halo columns are patched from the other end; with pressure-driven ends it also applies the
+// crossing corrections).  The model: block b, of rank k = b / n_sm (blocks fill the SMs rank by
+// rank), runs at speed 1 + skew (R-1-k)/(R-1) for R CTAs per SM; strip j costs f_j per row (f for
+// the two edge strips, 1 inside).  A bisection finds the smallest common duration T for which
+// dealing consecutive blocks to the strips in order -- each strip takes blocks until their speeds
+// cover ny f_j / T -- needs at most R n_sm blocks; each strip's rows are then split in proportion
+// to its blocks' speeds.  Items keep at least 8 rows on average (at most ny / 8 per strip).
+struct MarchModel {
+    double skew, fedge;
+};
+
+// Constants measured at 4096 x 4096 (GLUPS of the whole step over the tried values):
+//   BF16 (issue-bound): skew 0 / 0.12 / 0.2 / 0.28 / 0.36 / 0.45 -> 73.7 / 75.2 / 75.6 / 75.9 / 76.1 /
+//     73.6 with f = 1.09-1.2; pressure-driven ends f = 1.3 / 1.5 / 1.6 / 1.9 -> 62.2 / 65.6 / 64.8 / 63.6;
+//   FP32 (HBM-bound): any skew loses (0 / 0.04 / 0.12 / 0.2 -> 59.3 / 58.5 / 55.5 / 54.3: the later
+//     CTAs speed up once the earlier ones leave the memory system to them); f = 1.12-1.4 -> 59.3,
+//     pressure-driven ends f = 1.5 / 1.7 / 2.0 -> 54.4 / 52.5 / 52.4.
+static MarchModel march_model(int prec, bool gpbc) {
+    if (prec == LB_PREC_BF16) return {0.30, gpbc ? 1.5 : 1.15};
+    return {0.0, gpbc ? 1.5 : 1.2};
+}
+
+static std::vector<MarchItem> march_plan(int nx, int ny, int R, int nsm, MarchModel m) {
+    const int strips = nx / kMarchW;
+    const int slots = R * nsm;
+    const int maxn = std::max(1, ny / 8);
+    auto speed = [&](int b) {
+        const int k = std::min(b / nsm, R - 1);
+        return 1.0 + (R > 1 ? m.skew * (R - 1 - k) / (R - 1) : 0.0);
+    };
+    auto cost = [&](int s) { return (s == 0 || s == strips - 1) ? m.fedge : 1.0; };
+    auto deal = [&](double T, std::vector<int>* nper) {
+        int b = 0;
+        for (int s = 0; s < strips; ++s) {
+            const double need = ny * cost(s) / T;
+            double acc = 0.0;
+            int n = 0;
+            while (n < maxn && acc < need) acc += speed(b + n++);
+            if (nper) nper->push_back(n);
+            b += n;
+        }
+        return b;
+    };
+    std::vector<int> nper;
+    if (strips >= slots) {
+        nper.assign(strips, 1);  // more strips than resident CTAs: one item per strip
+    } else {
+        double lo = 1e-9, hi = 2.0 * ny * std::max(1.0, m.fedge);  // deal(hi) takes one block per strip
+        if (deal(lo, nullptr) <= slots) {
+            hi = lo;  // even the finest cut fits
+        } else {
+            for (int it = 0; it < 100; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (deal(mid, nullptr) <= slots) hi = mid;
+                else lo = mid;
+            }
+        }
+        deal(hi, &nper);
+    }
+    std::vector<MarchItem> items;
+    int b = 0;
+    for (int s = 0; s < strips; ++s) {
+        const int n = nper[s];
+        double tot = 0.0;
+        for (int k = 0; k < n; ++k) tot += speed(b + k);
+        double cum = 0.0;
+        int y = 0;
+        for (int k = 0; k < n; ++k) {
+            cum += speed(b + k);
+            const int y1 = k == n - 1 ? ny : (int)std::llround(ny * cum / tot);
+            MarchItem it{};
+            it.x0 = s * kMarchW;
+            it.y0 = y;
+            it.y1 = y1;
+            items.push_back(it);
+            y = y1;
+        }
+        b += n;
+    }
+    return items;
+}
+
 // Row-march plan: strips of kMarchW columns; the rows split into balanced chunks so that the
 // work items fill one wave of resident CTAs.
 lb_status plan_march(lb_handle* h) {
@@ -592,27 +681,8 @@ lb_status plan_march(lb_handle* h) {
     }
     if (e != cudaSuccess) return cuda_fail(e, "lb_create: march occupancy");
     if (bps < 1) return LB_OK;
-    const int strips = h->nx / kMarchW;
     const int slots = bps * nsm;
-    // one wave: at most as many items as resident CTAs (a partial second wave would double the
-    // kernel time for a few CTAs).  With pressure-driven ends the two edge strips do extra work
-    // per row (the boundary-column shifts), so they get rows ranges half as long.
-    const bool split_edges = h->gpbc && strips > 1;
-    int chunks = slots / (strips + (split_edges ? 2 : 0));
-    if (chunks > h->ny[0] / 8) chunks = h->ny[0] / 8;
-    if (chunks < 1) chunks = 1;
-    const int echunks = split_edges ? std::max(chunks, std::min(2 * chunks, h->ny[0] / 8)) : chunks;
-    std::vector<MarchItem> items;
-    for (int s = 0; s < strips; ++s) {
-        const int n = (s == 0 || s == strips - 1) ? echunks : chunks;
-        for (int c = 0; c < n; ++c) {
-            MarchItem it{};
-            it.x0 = s * kMarchW;
-            it.y0 = (int)((long long)h->ny[0] * c / n);
-            it.y1 = (int)((long long)h->ny[0] * (c + 1) / n);
-            items.push_back(it);
-        }
-    }
+    const std::vector<MarchItem> items = march_plan(h->nx, h->ny[0], bps, nsm, march_model(h->prec, h->gpbc));
     LB_CK(cudaMalloc(&h->march_items_d, sizeof(MarchItem) * items.size()));
     LB_CK(cudaMemcpy(h->march_items_d, items.data(), sizeof(MarchItem) * items.size(), cudaMemcpyHostToDevice));
     h->n_march_items = (int)items.size();
@@ -1554,6 +1624,22 @@ lb_status lb_set_wait_limit(lb_handle* h, double seconds) {
 
 long lb_step_count(const lb_handle* h) { return h ? h->step : -1; }
 int lb_uses_row_march(const lb_handle* h) { return (h && h->march) ? 1 : 0; }
+
+int lb_row_march_plan(int nx, int ny, int ctas_per_sm, int n_sm, int precision, int gpbc, int* items, int max_items) {
+    if (nx <= 0 || nx % kMarchW != 0 || ny < 16 || ctas_per_sm < 1 || n_sm < 1 || max_items < 0 ||
+        (precision != LB_PREC_F32 && precision != LB_PREC_BF16))
+        return -LB_EINVAL;
+    const std::vector<MarchItem> v = march_plan(nx, ny, ctas_per_sm, n_sm, march_model(precision, gpbc != 0));
+    if (items) {
+        if ((int)v.size() > max_items) return -LB_EINVAL;
+        for (size_t i = 0; i < v.size(); ++i) {
+            items[3 * i] = v[i].x0;
+            items[3 * i + 1] = v[i].y0;
+            items[3 * i + 2] = v[i].y1;
+        }
+    }
+    return (int)v.size();
+}
 long lb_graph_replays(const lb_handle* h) { return h ? h->graph_replays : -1; }
 size_t lb_num_nodes(const lb_handle* h) { return h ? (size_t)h->nodes : 0; }
 

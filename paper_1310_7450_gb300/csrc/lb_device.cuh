@@ -240,12 +240,21 @@ __device__ __forceinline__ void gradient_velocity(const C (&d)[9], C gx, C& dR, 
 // With n^eq_i(rho, j) = w_i [rho + 3 c.j + (4.5 (c.j)^2 - 1.5 j^2) / rho] the rebuilt value is
 // n*_i + w_i [delta - (4.5 (c.j)^2 - 1.5 j^2) delta / (rho_s (rho_s + delta))].  rho_s and j_s
 // are the moments of the node's post-collision populations (the shortened forcing keeps both).
+// The bracket depends only on the node left behind (its row, column and the direction), so a
+// kernel may evaluate it once per boundary node and direction; gpbc_add applies it with one
+// explicit fused multiply-add, which every kernel shares (bit-identical results whichever kernel
+// evaluated the bracket).
 template <typename C>
-__device__ __forceinline__ C gpbc_shift(int i, C rho_s_m1, C jx, C jy, C delta) {
+__device__ __forceinline__ C gpbc_shift_core(int i, C rho_s_m1, C jx, C jy, C delta) {
     const C rho_s = C(1) + rho_s_m1;
     const C cj = C(cx(i)) * jx + C(cy(i)) * jy;
     const C q = C(4.5) * cj * cj - C(1.5) * (jx * jx + jy * jy);
-    return wgt<C>(i) * (delta - q * Arith<C>::div(delta, rho_s * (rho_s + delta)));
+    return delta - q * Arith<C>::div(delta, rho_s * (rho_s + delta));
+}
+template <typename C>
+__device__ __forceinline__ void gpbc_add(C& n, int i, C core) {
+    if constexpr (sizeof(C) == 8) n = __fma_rn(wgt<C>(i), core, n);
+    else n = __fmaf_rn(wgt<C>(i), core, n);
 }
 
 // Moving wall on the last row (Zou and He): the populations arriving from beyond the wall

@@ -201,6 +201,11 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
 
     __shared__ int s_bad;  // set by any thread whose bounded wait gave up; read after a barrier
     __shared__ C s_delta[2];  // BND == 1 with GPBC: rho_out - mean(x = 0), rho_in - mean(x = nx-1)
+    // BND == 1 with GPBC: the bracket of the end-crossing rebuild (gpbc_shift_core) of every
+    // population that leaves a boundary column across the end, per source row (ring of 8 rows),
+    // boundary column c (0: x = 0, directions 3, 6, 7; 1: x = nx-1, directions 1, 5, 8) and
+    // direction; six lanes of an edge strip fill one row, the pulls read it
+    __shared__ C s_shift[BND == 1 ? 8 : 1][2][3];
     constexpr int TI = NT - 1;  // the thread that issues the copies (last lane; warp 0 computes
                                 // the halo columns)
     constexpr int TP = NT - 2;  // the thread that issues the L2 prefetches of residual steps
@@ -261,6 +266,25 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
         auto patch_store = [&](int r, T v) {
             if (r >= 0 && r < ny && r <= rlast) const_cast<T*>(slot_ptr(idx_of(r)))[pi * SW + ps] = v;
         };
+        // GPBC brackets: lanes 0..5 of the left edge strip's patchers (32..37 on a right edge
+        // strip) take one (boundary column, direction) each and evaluate source row r from the
+        // slots, which hold the column's raw stored populations (the strip's own edge column, or
+        // the halo image of the other end, patched before)
+        const bool gpbc_edge = BND == 1 && (left_edge || right_edge) && a.gcol != nullptr;  // CTA-uniform
+        const int sl = left_edge ? t : t - 32;
+        const bool shifter = gpbc_edge && sl >= 0 && sl < 6;
+        auto shift_row = [&](int r) {
+            if (r < 0 || r >= ny || r > rlast) return;
+            const int c = sl / 3, j = sl - 3 * (sl / 3);
+            const int i = c == 1 ? (j == 0 ? 1 : (j == 1 ? 5 : 8)) : (j == 0 ? 3 : (j == 1 ? 6 : 7));
+            const int bcol = c == 1 ? (right_edge ? CW - 1 : -1) : (left_edge ? 0 : CW);
+            const T* sb = slot_ptr(idx_of(r)) + HP + bcol;
+            C e[9], mR, mx, my;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) e[k] = (C)Store<T>::cvt(sb[k * SW]);
+            moments<C>(e, mR, mx, my);
+            s_shift[BND == 1 ? (r & 7) : 0][c][j] = gpbc_shift_core<C>(i, mR, mx, my, s_delta[c]);
+        };
         // pulled populations of node (col, r) from the slots (col relative to x0, may be -1 or CW):
         // direction i comes from source row r - cy_i, column col - cx_i
         auto pull = [&](int col, int r, C (&d)[9]) {
@@ -286,35 +310,23 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
                 }
             }
             if constexpr (BND == 1) {
-                if ((left_edge || right_edge) && a.gcol != nullptr) {
+                if (gpbc_edge) {
                     // the node's true column; the slots hold the raw periodic images, so every
-                    // population that crosses an end gets its shift here (Sec. II B)
+                    // population that crosses an end gets its shift here (Sec. II B):
+                    // populations entering x = 0 move with c_x = +1 and leave the column
+                    // x = nx-1 (boundary column c = 1); those entering x = nx-1 move with
+                    // c_x = -1 and leave x = 0 (c = 0)
                     const int xg = x0 + col;
                     const int X = xg < 0 ? xg + nx : (xg >= nx ? xg - nx : xg);
-                    if (X == 0 || X == nx - 1) {
-                        // populations entering at x = 0 move with c_x = +1 and leave the column
-                        // x = nx-1 (boundary column c = 1); those entering at x = nx-1 move with
-                        // c_x = -1 and leave x = 0 (c = 0).  The column data of the three source
-                        // rows are loaded together, before any shift is formed.
-                        const int c = X == 0 ? 1 : 0;
-                        const int sx = X == 0 ? 1 : -1;
-                        const C delta = s_delta[c];
-                        const C* gc = a.gcol + P.row_off + c * a.gny;
-                        C gr[3], gjx[3], gjy[3];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {  // source row r - 1 + k, k = 1 - c_y
-                            const int ys = r - 1 + k;
-                            const bool in = ys >= 0 && ys < ny;
-                            gr[k] = in ? gc[ys] : C(0);
-                            gjx[k] = in ? gc[2 * a.gny + ys] : C(0);
-                            gjy[k] = in ? gc[4 * a.gny + ys] : C(0);
-                        }
-#pragma unroll
-                        for (int i = 1; i < 9; ++i) {
-                            const int ys = r - cy(i);
-                            if (cx(i) != sx || ys < 0 || ys >= ny) continue;
-                            d[i] += gpbc_shift<C>(i, gr[1 - cy(i)], gjx[1 - cy(i)], gjy[1 - cy(i)], delta);
-                        }
+                    // (direction indices fixed per end: one lane runs this for the whole CTA)
+                    if (X == 0) {  // from x = nx-1: directions 1, 5, 8 (source rows r, r-1, r+1)
+                        gpbc_add<C>(d[1], 1, s_shift[r & 7][1][0]);
+                        if (r > 0) gpbc_add<C>(d[5], 5, s_shift[(r - 1) & 7][1][1]);
+                        if (r < ny - 1) gpbc_add<C>(d[8], 8, s_shift[(r + 1) & 7][1][2]);
+                    } else if (X == nx - 1) {  // from x = 0: directions 3, 6, 7
+                        gpbc_add<C>(d[3], 3, s_shift[r & 7][0][0]);
+                        if (r > 0) gpbc_add<C>(d[6], 6, s_shift[(r - 1) & 7][0][1]);
+                        if (r < ny - 1) gpbc_add<C>(d[7], 7, s_shift[(r + 1) & 7][0][2]);
                     }
                 }
             }
@@ -371,6 +383,11 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
         }
         __syncthreads();
         if (s_bad) { bad = true; break; }
+        if (gpbc_edge) {  // brackets of the rows waited and patched so far (CTA-uniform branch)
+            if (shifter)
+                for (int r = rbase; r <= rbase + 5; ++r) shift_row(r);
+            __syncthreads();
+        }
         {
             C dtmp[NC][9], a0[NC], a1[NC], a2[NC];
             moments_row(y0 - 1, dtmp, a0, a1, a2);
@@ -456,6 +473,10 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
                 fence_proxy_async();
                 issue(idx_of(y + K), x0, y + K);
             }
+            // brackets of row y+4: its copy was waited by the shifter lanes (patchers) and its
+            // halo patched before the barrier above; the first pull that reads it is that of
+            // row y+3, two barriers later
+            if (shifter && y + 4 <= rlast) shift_row(y + 4);
             // 3. collision of row y, node by node, then the row's stores
             {
                 const long long pn = (long long)y * nx + x;  // first own node

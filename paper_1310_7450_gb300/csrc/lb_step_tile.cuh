@@ -47,8 +47,8 @@ __device__ __forceinline__ void pull9(const T* __restrict__ pc, long long P, int
                 // crossing the end of the channel: rebuilt from the node it leaves (column
                 // c = 1 for x = nx-1 when entering the inlet, c = 0 when entering the outlet)
                 const int c = xr < 0 ? 1 : 0;
-                d[i] += gpbc_shift<C>(i, g.col[c * g.gny + ys], g.col[(2 + c) * g.gny + ys],
-                                      g.col[(4 + c) * g.gny + ys], xr < 0 ? g.dplus : g.dminus);
+                gpbc_add<C>(d[i], i, gpbc_shift_core<C>(i, g.col[c * g.gny + ys], g.col[(2 + c) * g.gny + ys],
+                                                        g.col[(4 + c) * g.gny + ys], xr < 0 ? g.dplus : g.dminus));
             }
         }
     }

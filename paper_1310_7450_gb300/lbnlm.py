@@ -107,6 +107,7 @@ def load():
         "lb_sweep_tune": ([_H], c_int),
         "lb_field_monitor_static": ([c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p], c_int),
         "lb_uses_row_march": ([_H], c_int),
+        "lb_row_march_plan": ([c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, c_int], c_int),
         "lb_graph_replays": ([_H], c_long),
         "lb_num_nodes": ([_H], c_size_t),
         "lb_destroy": ([_H], None),
@@ -357,6 +358,21 @@ def lb_step_count(h: int) -> int:
 
 def lb_uses_row_march(h: int) -> bool:
     return bool(load().lb_uses_row_march(h))
+
+
+def lb_row_march_plan(nx: int, ny: int, ctas_per_sm: int, n_sm: int, precision="f32", gpbc: bool = False) -> np.ndarray:
+    """The row-march kernel's work items for a single nx x ny channel: an int32 array [n, 3] of
+    (x0, y0, y1) (host computation; no GPU needed)."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    lib = load()
+    n = lib.lb_row_march_plan(nx, ny, ctas_per_sm, n_sm, prec, int(bool(gpbc)), None, 0)
+    if n < 0:
+        _check(-n, "lb_row_march_plan")
+    out = np.zeros((max(n, 1), 3), dtype=np.int32)
+    m = lib.lb_row_march_plan(nx, ny, ctas_per_sm, n_sm, prec, int(bool(gpbc)), out.ctypes.data, n)
+    if m < 0:
+        _check(-m, "lb_row_march_plan")
+    return out[:m]
 
 
 def lb_graph_replays(h: int) -> int:
