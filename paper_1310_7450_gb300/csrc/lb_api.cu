@@ -250,54 +250,40 @@ __global__ void k_set_fields(T* pop, C* drho, C* sig3, const double* u, const do
     }
 }
 
-// Apply the per-channel body forces (gx[0..n_ch)) and moving-wall velocities (gx[n_ch..2 n_ch))
-// staged in gx (device, copied from pinned host memory).
+// Apply the per-channel body forces (staged[0..n_ch)) and moving-wall velocities
+// (staged[n_ch..2 n_ch)), read straight from the pinned host staging slot (mapped), and keep a
+// device copy in gx for the kernels that read the drive there.
 template <typename C>
-__global__ void k_apply_gx(ChanParams<C>* chan, const double* gx, int n_ch, int nx) {
+__global__ void k_apply_gx(ChanParams<C>* chan, double* gx, const double* staged, int n_ch, int nx) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_ch) return;
-    chan[c].u_wall = (C)gx[n_ch + c];  // staged after the forces: the moving-wall velocities
+    const double g = staged[c], uw = staged[n_ch + c];
+    gx[c] = g;
+    gx[n_ch + c] = uw;
+    chan[c].u_wall = (C)uw;  // staged after the forces: the moving-wall velocities
     if (chan[c].gpbc) {  // pressure-driven: g sets the ghost densities, there is no body force
-        const double half = 1.5 * gx[c] * (double)(nx + 1);
+        const double half = 1.5 * g * (double)(nx + 1);
         chan[c].rho_in = (C)((double)chan[c].rho0_m1 + half);
         chan[c].rho_out = (C)((double)chan[c].rho0_m1 - half);
     } else {
-        chan[c].gx = (C)gx[c];
+        chan[c].gx = (C)g;
     }
 }
 
-// Per-channel reduction of the step's block partials, in a fixed order (deterministic).
+// Copy n doubles from device memory to mapped pinned host memory (the monitor's way back: a
+// kernel's stores reach the host without a copy-engine transfer in the stream).
+__global__ void k_copy_to_host(const double* src, double* dst, int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+// Per-channel reduction of the step's block partials, one warp per channel in a fixed order
+// (deterministic; the row-march kernel forms the same values itself, see monitor_reduce_warp).
 // with_residual = 0: the partials hold flux and max |u| only (F_MON); the residual slot reads -1
 __global__ void k_reduce_residual(const double* partials, const int* item_begin, const int* status, double* mon,
                                   int nx, long long state_index, int with_residual) {
     const int c = blockIdx.x;
-    const int b = item_begin[c], e = item_begin[c + 1];
-    __shared__ double red[kThreads][4];
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
-        s0 += partials[4 * k];
-        s1 += partials[4 * k + 1];
-        s2 += partials[4 * k + 2];
-        s3 = fmax(s3, partials[4 * k + 3]);
-    }
-    red[threadIdx.x][0] = s0; red[threadIdx.x][1] = s1; red[threadIdx.x][2] = s2; red[threadIdx.x][3] = s3;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) {
-            red[threadIdx.x][0] += red[threadIdx.x + h][0];
-            red[threadIdx.x][1] += red[threadIdx.x + h][1];
-            red[threadIdx.x][2] += red[threadIdx.x + h][2];
-            red[threadIdx.x][3] = fmax(red[threadIdx.x][3], red[threadIdx.x + h][3]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const bool ok = status[c] == 0;
-        mon[4 * c + 0] = !ok ? NAN : (!with_residual ? -1.0 : (red[0][1] > 0 ? sqrt(red[0][0] / red[0][1]) : 0.0));
-        mon[4 * c + 1] = ok ? red[0][2] / nx : NAN;
-        mon[4 * c + 2] = ok ? red[0][3] : NAN;
-        mon[4 * c + 3] = (double)state_index;
-    }
+    monitor_reduce_warp(partials, item_begin[c], item_begin[c + 1], status[c], mon + 4 * c, nx, state_index,
+                        with_residual, threadIdx.x);
 }
 
 template <typename A, typename B>
@@ -392,8 +378,12 @@ struct lb_handle {
     long mon_state = -1;       // state index of the last monitor evaluation (-1: none)
     bool mon_resid = false;    // the last monitor evaluation includes the residual
     int monitor_mode = 0;      // LB_MONITOR_RESIDUAL or LB_MONITOR_FLUX_MAX
-    int* status_h = nullptr;   // pinned
+    int* status_h = nullptr;   // pinned, mapped (row march: the kernel's status mirror)
+    int* status_hd = nullptr;  // its device address
     double* gx_h = nullptr;              // pinned staging of the drive: kDriveRing slots of 2 n_ch
+    double* gx_hd = nullptr;             // its device address (mapped)
+    double* mon_h = nullptr;             // mapped pinned copy of the monitor for lb_monitor
+    double* mon_hd = nullptr;
     cudaEvent_t gx_ev[kDriveRing] = {};  // values, each reused once its previous copy has run
     bool gx_pending[kDriveRing] = {};
     int gx_slot = 0;
@@ -432,6 +422,7 @@ struct lb_handle {
     void* gcol = nullptr;  // boundary-column moments and means (see StepArgs::gcol)
     double* gpart = nullptr;    // per-block partial sums of the column kernel
     unsigned* gcount = nullptr; // per-column block counters (zero between launches)
+    unsigned* done_count_d = nullptr;  // row-march CTAs done with the launch (zero between launches)
     int gpbc_max_ny = 0;
     int gny = 0;           // sum of ny over the channels
     std::vector<int> row_off;
@@ -756,8 +747,10 @@ void release(lb_handle* h) {
     free_dev(h->gcol);
     free_dev(h->gpart);
     free_dev(h->gcount);
+    free_dev(h->done_count_d);
     if (h->status_h) cudaFreeHost(h->status_h);
     if (h->gx_h) cudaFreeHost(h->gx_h);
+    if (h->mon_h) cudaFreeHost(h->mon_h);
     if (h->status_ev) cudaEventDestroy(h->status_ev);
     for (int k = 0; k < kDriveRing; ++k)
         if (h->gx_ev[k]) cudaEventDestroy(h->gx_ev[k]);
@@ -810,10 +803,11 @@ StepArgs<T, C> base_args(lb_handle* h) {
     return a;
 }
 
-// Body forces and wall velocities: host -> pinned staging -> device -> channel table, all
-// stream-ordered.  The staging is a ring of kDriveRing slots, and a slot is reused only after its
-// previous copy ran, so a host that changes the drive every step runs up to kDriveRing steps
-// ahead of the device instead of waiting for the step before.
+// Body forces and wall velocities: host -> pinned staging (mapped) -> channel table by one small
+// kernel that reads the staging slot itself, stream-ordered.  The staging is a ring of
+// kDriveRing slots, and a slot is reused only after the kernel that read it ran, so a host that
+// changes the drive every step runs up to kDriveRing steps ahead of the device instead of waiting
+// for the step before.
 lb_status push_drive(lb_handle* h) {
     const int k = h->gx_slot;
     h->gx_slot = (k + 1) % kDriveRing;
@@ -823,12 +817,12 @@ lb_status push_drive(lb_handle* h) {
         st[c] = h->params[c].g_x;
         st[h->n_ch + c] = h->u_wall[c];
     }
-    LB_CK(cudaMemcpyAsync(h->gx_d, st, sizeof(double) * 2 * h->n_ch, cudaMemcpyHostToDevice, h->stream));
-    LB_CK(cudaEventRecord(h->gx_ev[k], h->stream));
-    h->gx_pending[k] = true;
-    if (h->csize == 8) k_apply_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->gx_d, h->n_ch, h->nx);
-    else k_apply_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->gx_d, h->n_ch, h->nx);
+    const double* sd = h->gx_hd + (size_t)k * 2 * h->n_ch;
+    if (h->csize == 8) k_apply_gx<double><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<double>*)h->chan, h->gx_d, sd, h->n_ch, h->nx);
+    else k_apply_gx<float><<<(h->n_ch + 255) / 256, 256, 0, h->stream>>>((ChanParams<float>*)h->chan, h->gx_d, sd, h->n_ch, h->nx);
     LB_CK(cudaGetLastError());
+    LB_CK(cudaEventRecord(h->gx_ev[k], h->stream));  // the slot is read by the kernel above
+    h->gx_pending[k] = true;
     return LB_OK;
 }
 
@@ -871,12 +865,24 @@ cudaError_t launch(lb_handle* h, const StepArgs<T, C>& a) {
     return launch_step_tile<T, C, 1>(a, n, h->smem, h->stream);
 }
 
+// The row-march kernel's last CTA mirrors the status word into mapped host memory every step and,
+// on monitor steps (F_RESID / F_MON), reduces the item partials into mon_d.
+void march_monitor(lb_handle* h, int flags, MarchCtl& ctl) {
+    const bool mon = (flags & (F_RESID | F_MON)) != 0;
+    ctl.done_count = h->done_count_d;
+    ctl.status_host = h->status_hd;
+    ctl.mon = mon ? (double*)h->mon_d : nullptr;
+    ctl.state_index = h->step;
+    ctl.with_residual = (flags & F_RESID) ? 1 : 0;
+}
+
 // The row-march kernel takes plain steps (no fields output, no residual reduction).
 template <typename T, typename C>
 cudaError_t launch_march(lb_handle*, const StepArgs<T, C>&) { return cudaErrorNotSupported; }
 template <>
 cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float>& a) {
     MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0], h->wait_ns};
+    march_monitor(h, a.flags, ctl);
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
     if (h->gpbc)
         return h->smode ? launch_step_march<float, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
@@ -890,6 +896,7 @@ cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float
 template <>
 cudaError_t launch_march<__nv_bfloat16, float>(lb_handle* h, const StepArgs<__nv_bfloat16, float>& a) {
     MarchCtl ctl{h->march_items_d, h->n_march_items, h->status_d, h->P[0], h->base[0], h->wait_ns};
+    march_monitor(h, a.flags, ctl);
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
     if (h->gpbc)
         return h->smode ? launch_step_march<__nv_bfloat16, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
@@ -982,9 +989,11 @@ lb_status run_steps(lb_handle* h, long n) {
         if (h->march) LB_CK((launch_march<T, C>(h, a)));
         else LB_CK((launch<T, C>(h, a)));
         if (mon) {
-            k_reduce_residual<<<h->n_ch, kThreads, 0, h->stream>>>(h->partials, h->march ? h->march_item_begin_d : h->item_begin_d,
-                                                                    h->status_d, h->mon_d, h->nx, h->step, resid ? 1 : 0);
-            LB_CK(cudaGetLastError());
+            if (!h->march) {  // (the row-march kernel's last CTA reduces its partials itself)
+                k_reduce_residual<<<h->n_ch, 32, 0, h->stream>>>(h->partials, h->item_begin_d, h->status_d, h->mon_d,
+                                                                 h->nx, h->step, resid ? 1 : 0);
+                LB_CK(cudaGetLastError());
+            }
             h->mon_state = h->step;
             h->mon_resid = resid;
         }
@@ -1008,6 +1017,12 @@ lb_status fields_pass(lb_handle* h, C* fu, C* fs, C* fr) {
 }
 
 lb_status poll_status(lb_handle* h, bool wait) {
+    if (h->march) {  // the row-march kernel stores the status word into mapped host memory itself
+        const int s = *(volatile const int*)h->status_h;
+        if (s & 1) h->any_unstable = true;
+        if (s & 2) h->any_timeout = true;
+        return LB_OK;
+    }
     if (h->status_pending) {
         cudaError_t q = wait ? cudaEventSynchronize(h->status_ev) : cudaEventQuery(h->status_ev);
         if (q == cudaSuccess) {
@@ -1521,6 +1536,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     LB_ALLOC(h->node_off_d, h->n_ch * sizeof(long long));
     LB_ALLOC(h->ny_d, h->n_ch * sizeof(int));
     LB_ALLOC(h->gx_d, 2 * h->n_ch * sizeof(double));
+    LB_ALLOC(h->done_count_d, sizeof(unsigned));
     if (h->gpbc) {
         for (int c = 0; c < h->n_ch; ++c) h->gpbc_max_ny = std::max(h->gpbc_max_ny, h->ny[c]);
         const size_t rb = ((size_t)h->gpbc_max_ny + 255) / 256;
@@ -1529,10 +1545,15 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
         LB_ALLOC(h->gcount, 2 * h->n_ch * sizeof(unsigned));
     }
 #undef LB_ALLOC
-    e = cudaMallocHost((void**)&h->status_h, h->n_ch * sizeof(int));
-    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
-    e = cudaMallocHost((void**)&h->gx_h, (size_t)kDriveRing * 2 * h->n_ch * sizeof(double));
-    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaMallocHost"));
+    e = cudaHostAlloc((void**)&h->status_h, h->n_ch * sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&h->status_hd, h->status_h, 0);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaHostAlloc (mapped)"));
+    std::memset(h->status_h, 0, h->n_ch * sizeof(int));
+    e = cudaHostAlloc((void**)&h->gx_h, (size_t)kDriveRing * 2 * h->n_ch * sizeof(double), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&h->gx_hd, h->gx_h, 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&h->mon_h, 4 * (size_t)h->n_ch * sizeof(double), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&h->mon_hd, h->mon_h, 0);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaHostAlloc (mapped)"));
     e = cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming);
     for (int k = 0; k < kDriveRing && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&h->gx_ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "lb_create: cudaEventCreate"));
@@ -1567,6 +1588,7 @@ lb_status lb_create(const lb_grid* grid, const lb_params* params, const lb_bound
     ok &= cudaMemcpy(h->gx_d, gx.data(), sizeof(double) * 2 * h->n_ch, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemsetAsync(h->status_d, 0, sizeof(int) * h->n_ch, h->stream) == cudaSuccess;
     if (h->gcount) ok &= cudaMemsetAsync(h->gcount, 0, 2 * h->n_ch * sizeof(unsigned), h->stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(h->done_count_d, 0, sizeof(unsigned), h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(h->uprev, 0, 2 * h->planes * h->csize, h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(h->popB, 0, 9 * h->planes * h->tsize, h->stream) == cudaSuccess;
     if (h->sig4) ok &= cudaMemsetAsync(h->sig4, 0, 4 * h->planes * h->csize, h->stream) == cudaSuccess;
@@ -1652,7 +1674,7 @@ lb_status lb_step(lb_handle* h, long n) {
     if (n == 0) return h->any_unstable ? LB_EUNSTABLE : LB_OK;
     st = with_types(h->prec, [&](auto tt, auto tc) { LB_TYPES(tt, tc); return run_steps<T, C>(h, n); });
     if (st != LB_OK) return st;
-    if (!h->status_pending) {
+    if (!h->march && !h->status_pending) {
         st = request_status(h);
         if (st != LB_OK) return st;
     }
@@ -1692,15 +1714,27 @@ lb_status lb_get_fields(lb_handle* h, void* u, void* sigma, void* rho, int out_d
 lb_status lb_monitor(lb_handle* h, double* out) {
     if (!h || !out) return fail(LB_EINVAL, "lb_monitor: null argument%s");
     if (h->mon_state < 0) return fail(LB_ESTATE, "lb_monitor: no monitor evaluated yet (run lb_step with n >= 2)%s");
-    LB_CK(cudaMemcpyAsync(out, h->mon_d, 4 * h->n_ch * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    k_copy_to_host<<<1, 128, 0, h->stream>>>(h->mon_d, h->mon_hd, 4 * h->n_ch);
+    LB_CK(cudaGetLastError());
     LB_CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(out, h->mon_h, 4 * h->n_ch * sizeof(double));
     return LB_OK;
 }
 
 lb_status lb_monitor_async(lb_handle* h, double* out) {
     if (!h || !out) return fail(LB_EINVAL, "lb_monitor_async: null argument%s");
     if (h->mon_state < 0) return fail(LB_ESTATE, "lb_monitor_async: no monitor evaluated yet (run lb_step with n >= 2)%s");
-    LB_CK(cudaMemcpyAsync(out, h->mon_d, 4 * h->n_ch * sizeof(double), cudaMemcpyDefault, h->stream));
+    // pinned host memory mapped into the device's address space (what cudaHostAlloc and
+    // torch's pin_memory give under unified addressing): a one-block kernel stores the values
+    // there; anything else (device memory, pageable host memory) takes a stream-ordered copy
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+        k_copy_to_host<<<1, 128, 0, h->stream>>>(h->mon_d, (double*)at.devicePointer, 4 * h->n_ch);
+        LB_CK(cudaGetLastError());
+    } else {
+        (void)cudaGetLastError();
+        LB_CK(cudaMemcpyAsync(out, h->mon_d, 4 * h->n_ch * sizeof(double), cudaMemcpyDefault, h->stream));
+    }
     return LB_OK;
 }
 
@@ -1972,6 +2006,7 @@ lb_status lb_set_state(lb_handle* h, const void* buf, size_t bytes) {
     LB_CK(cudaMemsetAsync(h->status_d, 0, sizeof(int) * h->n_ch, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     h->status_pending = false;
+    std::memset(h->status_h, 0, h->n_ch * sizeof(int));  // (the stream is idle: no kernel writes it now)
     h->any_unstable = h->any_timeout = false;
     h->step = hd.step;
     h->uprev_state = -10;

@@ -482,4 +482,50 @@ __device__ __forceinline__ bool velocity_ok(C jx, C jy, C rho_h, C guard) {
     return jx * jx + jy * jy <= guard * guard * rho_h * rho_h;
 }
 
+
+// Channel monitor from per-item partials (sum du^2, sum u^2, sum u_x, max |u|) of items [b, e):
+// one warp, lane l adding items b+l, b+l+32, ... in order, then a fixed butterfly, so every kernel
+// that forms it gives the same bits.  mon[0..3] = residual sqrt(sum du^2 / sum u^2) (-1 without
+// it), mean flux per column, max |u|, state index; NaN diagnostics when the channel's status is
+// set.  The partials are read through L2 (they may come from other CTAs of the same kernel).
+__device__ __forceinline__ void monitor_reduce_warp(const double* partials, int b, int e, int status, double* mon,
+                                                    int nx, long long state_index, int with_residual, int lane) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    constexpr int U = 8;  // items per lane loaded together (one round trip to L2 per batch)
+    for (int k0 = b + lane; k0 < e; k0 += 32 * U) {
+        double2 v[U][2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + 32 * u;
+            if (k < e) {
+                v[u][0] = __ldcg(reinterpret_cast<const double2*>(partials + 4 * k));
+                v[u][1] = __ldcg(reinterpret_cast<const double2*>(partials + 4 * k + 2));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (k0 + 32 * u < e) {
+                s0 += v[u][0].x;
+                s1 += v[u][0].y;
+                s2 += v[u][1].x;
+                s3 = fmax(s3, v[u][1].y);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 = fmax(s3, __shfl_xor_sync(0xffffffffu, s3, o));
+    }
+    if (lane == 0) {
+        const bool ok = status == 0;
+        mon[0] = !ok ? NAN : (!with_residual ? -1.0 : (s1 > 0 ? sqrt(s0 / s1) : 0.0));
+        mon[1] = ok ? s2 / nx : NAN;
+        mon[2] = ok ? s3 : NAN;
+        mon[3] = (double)state_index;
+    }
+}
+
 }  // namespace lbk

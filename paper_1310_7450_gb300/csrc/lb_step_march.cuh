@@ -38,6 +38,14 @@ struct MarchCtl {
     long long plane;    // plane stride of the channel's fields (elements)
     long long base;     // plane offset of the channel (its planes start at k * base)
     unsigned long long max_wait_ns;  // limit of every mbarrier wait (0: one non-blocking probe)
+    // the last CTA to finish (done_count counts them; zero between launches) stores the channel's
+    // status word into status_host (mapped pinned host memory: the host polls it without a copy
+    // in the stream) and, on monitor steps (mon set), reduces the item partials into mon[0..3]
+    unsigned* done_count = nullptr;
+    int* status_host = nullptr;
+    double* mon = nullptr;
+    long long state_index = 0;
+    int with_residual = 0;
 };
 
 // A CTA whose wait gave up waits this long for its own copies in flight before it returns.  A
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
     const int t = threadIdx.x;
     const ChanParams<C> P = a.chan[0];
     const int nx = a.nx, ny = P.ny;
-    if (a.status[0] != 0) return;
+    const bool halted = a.status[0] != 0;  // an unstable or timed-out channel takes no more steps
 
     __shared__ int s_bad;  // set by any thread whose bounded wait gave up; read after a barrier
     __shared__ C s_delta[2];  // BND == 1 with GPBC: rho_out - mean(x = 0), rho_in - mean(x = nx-1)
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
         last_issued[idx % K] = idx;
     };
 
-    for (int item = blockIdx.x; item < ctl.n_items && !bad; item += gridDim.x) {
+    for (int item = blockIdx.x; item < ctl.n_items && !bad && !halted; item += gridDim.x) {
         const MarchItem it = ctl.items[item];
         const int x0 = it.x0, y0 = it.y0, y1 = it.y1;
         const int rbase = y0 - 2;                 // first source row of this item
@@ -605,6 +613,25 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
                 if (last_issued[k] != 0xffffffffu) mbar_wait(&bars[k], (last_issued[k] / K) & 1u, kMarchDrainNs);
         }
         __syncthreads();
+    }
+    if (ctl.done_count != nullptr) {  // the last CTA to get here: status mirror and monitor
+        __shared__ bool s_last;
+        __syncthreads();
+        if (t == 0) {
+            __threadfence();  // this CTA's partials and status bits before its count
+            s_last = atomicAdd(ctl.done_count, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last && t < 32) {
+            __threadfence();
+            const int st = *(volatile const int*)a.status;
+            if (ctl.mon != nullptr)
+                monitor_reduce_warp(a.partials, 0, ctl.n_items, st, ctl.mon, nx, ctl.state_index, ctl.with_residual, t);
+            if (t == 0) {
+                if (ctl.status_host != nullptr) *(volatile int*)ctl.status_host = st;
+                *ctl.done_count = 0u;
+            }
+        }
     }
 }
 
