@@ -562,28 +562,36 @@ bool make_pop_map(const lb_handle* h, void* base, CUtensorMap* map) {
 // Items are not equally long, because CTAs are not equally fast: the warp schedulers favour older
 // warps, so the CTAs that arrive later on an SM take longer for the same rows (measured at
 // 4096 x 4096 with equal items, per CTA rank on its SM: FP32 five ranks 246 ... 275 us; BF16
-// eight ranks 182 ... 219 us; only the BF16 step gains from dealing rows by rank, see the
-// constants below), and an edge strip costs more per row than an interior one (its
+// eight ranks 182 ... 219 us), and an edge strip costs more per row than an interior one (its
 // halo columns are patched from the other end; with pressure-driven ends it also applies the
 // crossing corrections).  The model: block b, of rank k = b / n_sm (blocks fill the SMs rank by
 // rank), runs at speed 1 + skew (R-1-k)/(R-1) for R CTAs per SM; strip j costs f_j per row (f for
-// the two edge strips, 1 inside).  A bisection finds the smallest common duration T for which
-// dealing consecutive blocks to the strips in order -- each strip takes blocks until their speeds
-// cover ny f_j / T -- needs at most R n_sm blocks; each strip's rows are then split in proportion
-// to its blocks' speeds.  Items keep at least 8 rows on average (at most ny / 8 per strip).
+// the two edge strips, 1 inside).  A bisection finds the smallest common duration T whose dealing
+// needs at most R n_sm blocks; rows are then split in proportion to the blocks' speeds.  Two
+// dealings:
+//  - strip-major: each strip takes consecutive blocks until their speeds cover ny f_j / T;
+//  - chunk-major: the edge strips first, the same way, then the interior strips share their row
+//    boundaries -- row chunk c of every interior strip on consecutive blocks, T times the speed of
+//    the slowest of them in rows -- so neighbouring strips march the same rows at the same time
+//    and read each other's halo columns from L2 (with boundaries that differ between strips, BF16
+//    re-reads 9 DRAM bytes per node of halo).
+// Items keep at least 8 rows on average (at most ny / 8 per strip).
 struct MarchModel {
     double skew, fedge;
+    bool chunk_major;
 };
 
-// Constants measured at 4096 x 4096 (GLUPS of the whole step over the tried values):
-//   BF16 (issue-bound): skew 0 / 0.12 / 0.2 / 0.28 / 0.36 / 0.45 -> 73.7 / 75.2 / 75.6 / 75.9 / 76.1 /
-//     73.6 with f = 1.09-1.2; pressure-driven ends f = 1.3 / 1.5 / 1.6 / 1.9 -> 62.2 / 65.6 / 64.8 / 63.6;
-//   FP32 (HBM-bound): any skew loses (0 / 0.04 / 0.12 / 0.2 -> 59.3 / 58.5 / 55.5 / 54.3: the later
-//     CTAs speed up once the earlier ones leave the memory system to them); f = 1.12-1.4 -> 59.3,
-//     pressure-driven ends f = 1.5 / 1.7 / 2.0 -> 54.4 / 52.5 / 52.4.
+// Constants measured at 4096 x 4096 (GLUPS of the whole step; repeated runs on one GPU):
+//   FP32 (HBM-bound): chunk-major skew 0.12: 60.5 (0.08: 60.1, 0.16: 60.4, 0.2: 59.4, 0.3: 58.6)
+//     against strip-major skew 0: 59.1 (strip-major with skew loses: 0.12 -> 55.5, the halo
+//     re-reads); f = 1.2; pressure-driven ends f = 1.5 with the edge strips first 53.6 (last: 50.3;
+//     strip-major 53.0); moving wall 59.1 (57.7); 8192 x 2048 58.2 (57.2); 2048 x 2048 52.6 (51.9).
+//   BF16 (issue-bound): strip-major skew 0.3: 74.7 (chunk-major 74.0); skew 0 / 0.12 / 0.2 / 0.28 /
+//     0.36 / 0.45 -> 73.7 / 75.2 / 75.6 / 75.9 / 76.1 / 73.6 with f = 1.09-1.2; pressure-driven
+//     ends f = 1.3 / 1.5 / 1.6 / 1.9 -> 62.2 / 65.6 / 64.8 / 63.6.
 static MarchModel march_model(int prec, bool gpbc) {
-    if (prec == LB_PREC_BF16) return {0.30, gpbc ? 1.5 : 1.15};
-    return {0.0, gpbc ? 1.5 : 1.2};
+    if (prec == LB_PREC_BF16) return {0.30, gpbc ? 1.5 : 1.15, false};
+    return {0.12, gpbc ? 1.5 : 1.2, true};
 }
 
 static std::vector<MarchItem> march_plan(int nx, int ny, int R, int nsm, MarchModel m) {
@@ -595,59 +603,94 @@ static std::vector<MarchItem> march_plan(int nx, int ny, int R, int nsm, MarchMo
         return 1.0 + (R > 1 ? m.skew * (R - 1 - k) / (R - 1) : 0.0);
     };
     auto cost = [&](int s) { return (s == 0 || s == strips - 1) ? m.fedge : 1.0; };
-    auto deal = [&](double T, std::vector<int>* nper) {
-        int b = 0;
-        for (int s = 0; s < strips; ++s) {
-            const double need = ny * cost(s) / T;
-            double acc = 0.0;
-            int n = 0;
-            while (n < maxn && acc < need) acc += speed(b + n++);
-            if (nper) nper->push_back(n);
-            b += n;
-        }
-        return b;
-    };
-    std::vector<int> nper;
-    if (strips >= slots) {
-        nper.assign(strips, 1);  // more strips than resident CTAs: one item per strip
-    } else {
-        double lo = 1e-9, hi = 2.0 * ny * std::max(1.0, m.fedge);  // deal(hi) takes one block per strip
-        if (deal(lo, nullptr) <= slots) {
-            hi = lo;  // even the finest cut fits
-        } else {
-            for (int it = 0; it < 100; ++it) {
-                const double mid = 0.5 * (lo + hi);
-                if (deal(mid, nullptr) <= slots) hi = mid;
-                else lo = mid;
-            }
-        }
-        deal(hi, &nper);
-    }
-    std::vector<MarchItem> items;
-    int b = 0;
-    for (int s = 0; s < strips; ++s) {
-        const int n = nper[s];
+    // the rows [0, ny) of one strip split in proportion to the weights w
+    auto split = [&](std::vector<MarchItem>& out, int x0, const std::vector<double>& w) {
         double tot = 0.0;
-        for (int k = 0; k < n; ++k) tot += speed(b + k);
+        for (double v : w) tot += v;
         double cum = 0.0;
         int y = 0;
-        for (int k = 0; k < n; ++k) {
-            cum += speed(b + k);
-            const int y1 = k == n - 1 ? ny : (int)std::llround(ny * cum / tot);
+        for (size_t k = 0; k < w.size(); ++k) {
+            cum += w[k];
+            const int y1 = k + 1 == w.size() ? ny : (int)std::llround(ny * cum / tot);
             MarchItem it{};
-            it.x0 = s * kMarchW;
+            it.x0 = x0;
             it.y0 = y;
             it.y1 = y1;
-            items.push_back(it);
+            out.push_back(it);
             y = y1;
         }
-        b += n;
+    };
+    // blocks from b on until their speeds cover ny f / T (at most maxn)
+    auto take = [&](double T, int b, double f) {
+        double acc = 0.0;
+        int n = 0;
+        while (n < maxn && acc < ny * f / T) acc += speed(b + n++);
+        return n;
+    };
+    const bool cm = m.chunk_major && strips >= 3 && strips < slots;
+    const int I = strips - 2;
+    // blocks per strip (strip-major) or [edge 0, edge 1, chunks] (chunk-major) at duration T
+    auto deal = [&](double T, std::vector<int>* out) {
+        int b = 0;
+        if (!cm) {
+            for (int s = 0; s < strips; ++s) {
+                const int n = strips >= slots ? 1 : take(T, b, cost(s));
+                if (out) out->push_back(n);
+                b += n;
+            }
+            return b;
+        }
+        for (int e = 0; e < 2; ++e) {
+            const int n = take(T, b, m.fedge);
+            if (out) out->push_back(n);
+            b += n;
+        }
+        int C = 0;
+        double acc = 0.0;
+        while (C < maxn && acc < ny) acc += T * speed(b + (++C) * I - 1);
+        if (out) out->push_back(C);
+        return b + C * I;
+    };
+    double lo = 1e-9, hi = 4.0 * ny * std::max(1.0, m.fedge);  // deal(hi): one block per strip
+    if (strips >= slots || deal(lo, nullptr) <= slots) {
+        hi = strips >= slots ? hi : lo;
+    } else {
+        for (int it = 0; it < 100; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (deal(mid, nullptr) <= slots) hi = mid;
+            else lo = mid;
+        }
     }
+    std::vector<int> n;
+    deal(hi, &n);
+    std::vector<MarchItem> items;
+    int b = 0;
+    auto strip_items = [&](int s, int cnt) {
+        std::vector<double> w(cnt);
+        for (int k = 0; k < cnt; ++k) w[k] = speed(b + k);
+        split(items, s * kMarchW, w);
+        b += cnt;
+    };
+    if (!cm) {
+        for (int s = 0; s < strips; ++s) strip_items(s, n[s]);
+        return items;
+    }
+    strip_items(0, n[0]);
+    strip_items(strips - 1, n[1]);
+    const int C = n[2];
+    std::vector<double> wc(C);
+    for (int c = 0; c < C; ++c) wc[c] = speed(b + (c + 1) * I - 1);
+    std::vector<MarchItem> chunk;
+    split(chunk, 0, wc);
+    for (int c = 0; c < C; ++c)
+        for (int s = 1; s <= I; ++s) {
+            MarchItem it = chunk[c];
+            it.x0 = s * kMarchW;
+            items.push_back(it);
+        }
     return items;
 }
 
-// Row-march plan: strips of kMarchW columns; the rows split into balanced chunks so that the
-// work items fill one wave of resident CTAs.
 lb_status plan_march(lb_handle* h) {
     h->march = false;
     if (h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
