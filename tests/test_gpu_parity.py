@@ -595,3 +595,55 @@ def test_cessation_stopping_signature_on_gpu(stream, prec):
     assert (tg[1e-4] - tg[1e-2]) / tg[1e-2] <= 0.35
     for lv in (1e-2, 1e-4):
         assert abs(tg[lv] - to[lv]) <= every
+
+
+def test_row_march_status_mirror_reports_instability_and_clears_on_restore(stream):
+    """The row-march kernel's last CTA stores the status word into mapped host memory; lb_step
+    reads that mirror without a copy in the stream.  A NaN planted on the host makes the next
+    lb_step after the stream drained return LB_EUNSTABLE with no synchronous status read in
+    between, and a restored checkpoint clears the mirror (the channel steps again)."""
+    import torch
+    nx, ny = 256, 40
+    p = dict(nlm(), rho_pert_amp=1e-3, seed=4)
+    with lbnlm.Channels(nx, ny, p, "f32", stream=stream) as sim:
+        assert lbnlm.lb_uses_row_march(sim.h)
+        assert sim.step(3) == lbnlm.LB_OK
+        buf = np.zeros(lbnlm.lb_state_bytes(sim.h), dtype=np.uint8)
+        lbnlm.lb_get_state(sim.h, buf)
+        (n, d), = sim.populations()
+        n = n.copy()
+        n[4, 17, 131] = np.nan
+        sim.set_populations([n], [d])
+        assert sim.step(2) == lbnlm.LB_OK          # (the instability is detected asynchronously)
+        torch.cuda.synchronize()
+        assert sim.step(1) == lbnlm.LB_EUNSTABLE   # from the mirror alone
+        assert list(sim.status()) == [1]
+        lbnlm.lb_set_state(sim.h, buf)
+        assert sim.step(4) == lbnlm.LB_OK
+        torch.cuda.synchronize()
+        assert sim.step(1) == lbnlm.LB_OK
+        assert np.all(np.isfinite(sim.monitor()[0][1:3]))
+
+
+@pytest.mark.parametrize("mode", [lbnlm.LB_MONITOR_FLUX_MAX, lbnlm.LB_MONITOR_RESIDUAL])
+def test_monitor_async_destinations_agree(stream, mode):
+    """lb_monitor_async writes mapped pinned host memory through a one-block kernel and anything
+    else (device memory, pageable host memory) through a stream-ordered copy; every destination
+    receives the values lb_monitor reports, bitwise, on the row-march and on the tile kernel."""
+    import torch
+    for nx, nys, prec in ((256, [48], "f32"), (6, [11, 17], "f64")):
+        ps = [dict(nlm(), rho_pert_amp=1e-3, seed=30 + k) for k in range(len(nys))]
+        with lbnlm.Channels(nx, nys, ps, prec, stream=stream) as sim:
+            lbnlm.lb_set_monitor_mode(sim.h, mode)
+            sim.step(7)
+            pinned = torch.zeros(4 * len(nys), dtype=torch.float64, pin_memory=True)
+            dev = torch.zeros(4 * len(nys), dtype=torch.float64, device="cuda")
+            pageable = np.zeros(4 * len(nys))
+            lbnlm.lb_monitor_async(sim.h, pinned)
+            lbnlm.lb_monitor_async(sim.h, dev)
+            lbnlm.lb_monitor_async(sim.h, pageable)
+            torch.cuda.synchronize()
+            want = sim.monitor().reshape(-1)
+            assert np.all(np.isfinite(want[1::4]))
+            for got in (pinned.numpy(), dev.cpu().numpy(), pageable):
+                assert np.array_equal(got, want)
