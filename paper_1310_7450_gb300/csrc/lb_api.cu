@@ -77,14 +77,17 @@ LB_SWEEP_EXTERN(float, float)
 LB_SWEEP_EXTERN(__nv_bfloat16, float)
 LB_SWEEP_EXTERN(double, double)
 #undef LB_SWEEP_EXTERN
-#define LB_SWEEP_SMEM_EXTERN(T, C)                                                                                   \
-    extern template cudaError_t launch_sweep_smem<T, C, 128, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
-    extern template cudaError_t launch_sweep_smem<T, C, 256, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
-    extern template cudaError_t launch_sweep_smem_capacity<T, C, 128, 4>(int, size_t, int*);                            \
-    extern template cudaError_t launch_sweep_smem_capacity<T, C, 256, 4>(int, size_t, int*);
-LB_SWEEP_SMEM_EXTERN(float, float)
-LB_SWEEP_SMEM_EXTERN(__nv_bfloat16, float)
-LB_SWEEP_SMEM_EXTERN(double, double)
+#define LB_SWEEP_SMEM_EXTERN(T, C, NX)                                                                                   \
+    extern template cudaError_t launch_sweep_smem<T, C, 128, 4, NX>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_sweep_smem<T, C, 256, 4, NX>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_sweep_smem_capacity<T, C, 128, 4, NX>(int, size_t, int*);                            \
+    extern template cudaError_t launch_sweep_smem_capacity<T, C, 256, 4, NX>(int, size_t, int*);
+LB_SWEEP_SMEM_EXTERN(float, float, 0)
+LB_SWEEP_SMEM_EXTERN(__nv_bfloat16, float, 0)
+LB_SWEEP_SMEM_EXTERN(double, double, 0)
+LB_SWEEP_SMEM_EXTERN(float, float, 4)
+LB_SWEEP_SMEM_EXTERN(__nv_bfloat16, float, 4)
+LB_SWEEP_SMEM_EXTERN(double, double, 4)
 #undef LB_SWEEP_SMEM_EXTERN
 extern template cudaError_t march_occupancy<float, float, 0>(int*);
 extern template cudaError_t march_occupancy<float, float, 1>(int*);
@@ -1139,6 +1142,10 @@ cudaError_t sweep_launch(lb_handle* h, const SweepGroup& g, int var, int nt, int
     a.sr_key = step_key(h, h->step + 0x5bd1e995ll);
     if (var == 1) {
         const size_t smem = sweep_smem_resident(h, g.ny_max, cl);
+        if (h->nx == 4) {  // the 4-column channels of the batched sweep: width known at compile time
+            if (nt == 128) return launch_sweep_smem<T, C, 128, kSweepNPT, 4>(a, g.count, cl, smem, stream);
+            return launch_sweep_smem<T, C, 256, kSweepNPT, 4>(a, g.count, cl, smem, stream);
+        }
         if (nt == 128) return launch_sweep_smem<T, C, 128, kSweepNPT>(a, g.count, cl, smem, stream);
         return launch_sweep_smem<T, C, 256, kSweepNPT>(a, g.count, cl, smem, stream);
     }
@@ -1165,6 +1172,9 @@ int sweep_capacity(lb_handle* h, const SweepGroup& g, int var, int nt, int cl) {
         else {
             if (var == 1) {
                 const size_t smem = sweep_smem_resident(h, g.ny_max, cl);
+                if (h->nx == 4)
+                    return nt == 128 ? launch_sweep_smem_capacity<T, C, 128, kSweepNPT, 4>(cl, smem, &n)
+                                     : launch_sweep_smem_capacity<T, C, 256, kSweepNPT, 4>(cl, smem, &n);
                 return nt == 128 ? launch_sweep_smem_capacity<T, C, 128, kSweepNPT>(cl, smem, &n)
                                  : launch_sweep_smem_capacity<T, C, 256, kSweepNPT>(cl, smem, &n);
             }

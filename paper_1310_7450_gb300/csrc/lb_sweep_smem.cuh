@@ -22,15 +22,19 @@
 
 namespace lbk {
 
-template <typename T, typename C, int NT, int NPT>
-__global__ void __launch_bounds__(NT) k_sweep_smem(const SweepArgs<T, C> a) {
+// NX > 0: the handle's width as a compile-time constant (the node index arithmetic of every step
+// becomes shifts and masks for NX = 4); NX = 0: any width, read from the arguments.
+template <typename T, typename C, int NT, int NPT, int NX = 0>
+// FP32 arithmetic: at most 128 registers (4 x 128 or 2 x 256 threads per SM; the width-4 kernel
+// would otherwise keep its loop-invariant node indices in 254); FP64: unbounded, as before.
+__global__ void __launch_bounds__(NT, sizeof(C) == 8 ? 1 : 512 / NT) k_sweep_smem(const SweepArgs<T, C> a) {
     constexpr int HR = 3;  // halo rows of populations on each side
     cg::cluster_group cluster = cg::this_cluster();
     const int CL = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int ch = a.order[blockIdx.x / CL];
     const ChanParams<C> P = a.chan[ch];
-    const int nx = a.nx, ny = P.ny, t = threadIdx.x;
+    const int nx = NX > 0 ? NX : a.nx, ny = P.ny, t = threadIdx.x;
     const int y0 = (int)((long long)ny * rank / CL), y1 = (int)((long long)ny * (rank + 1) / CL);
     const int yb = y0 - HR;                                  // global row of local row 0
     const int R = (y1 - y0) + 2 * HR;                        // local rows per buffer
@@ -185,7 +189,8 @@ __global__ void __launch_bounds__(NT) k_sweep_smem(const SweepArgs<T, C> a) {
         {
             const int nb_lo = y0 > 0 ? HR : 0;                 // halo rows below the own rows
             const int nb_hi = y1 < ny ? HR : 0;                // and above
-            const int n_copy = 9 * (nb_lo + nb_hi) * nx;
+            const int n_copy = 9 * (nb_lo + nb_hi) * nx;  // element e: column e % nx, then
+                                                          // direction (e / nx) % 9, halo row (e / nx) / 9
             // a neighbour's buffers start at the same shared-memory offset as ours, but its plane
             // stride follows its own row count
             const bool second = (s & 1) == 0;                  // `nxt` is the second buffer
@@ -207,8 +212,8 @@ __global__ void __launch_bounds__(NT) k_sweep_smem(const SweepArgs<T, C> a) {
                 nxt_hi = second ? base + 9 * PS_hi : base;
             }
             for (int e = t; e < n_copy; e += NT) {
-                const int i = e / ((nb_lo + nb_hi) * nx), rem = e % ((nb_lo + nb_hi) * nx);
-                const int hr = rem / nx, x = rem % nx;
+                const int x = e % nx, q = e / nx;
+                const int i = q % 9, hr = q / 9;
                 if (hr < nb_lo) {
                     const int y = y0 - HR + hr;
                     nxt[i * PS + (y - yb) * nx + x] = nxt_lo[i * PS_lo + (y - yb_lo) * nx + x];
@@ -271,9 +276,9 @@ constexpr size_t sweep_smem_bytes(int rows, int nx) {
 
 // How many clusters of `cl` CTAs with `smem` bytes the device can hold at once (0: the shape cannot
 // be co-scheduled, so it is never launched).
-template <typename T, typename C, int NT, int NPT>
+template <typename T, typename C, int NT, int NPT, int NX = 0>
 cudaError_t launch_sweep_smem_capacity(int cl, size_t smem, int* n_clusters) {
-    auto k = k_sweep_smem<T, C, NT, NPT>;
+    auto k = k_sweep_smem<T, C, NT, NPT, NX>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -292,9 +297,9 @@ cudaError_t launch_sweep_smem_capacity(int cl, size_t smem, int* n_clusters) {
     return cudaOccupancyMaxActiveClusters(n_clusters, k, &cfg);
 }
 
-template <typename T, typename C, int NT, int NPT>
+template <typename T, typename C, int NT, int NPT, int NX = 0>
 cudaError_t launch_sweep_smem(const SweepArgs<T, C>& a, int n_clusters, int cl, size_t smem, cudaStream_t s) {
-    auto k = k_sweep_smem<T, C, NT, NPT>;
+    auto k = k_sweep_smem<T, C, NT, NPT, NX>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
