@@ -68,14 +68,17 @@ extern template cudaError_t launch_step_march<float, float, 0>(const CUtensorMap
 extern template cudaError_t launch_step_march<float, float, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t launch_step_march<__nv_bfloat16, float, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
-#define LB_SWEEP_EXTERN(T, C)                                                                                   \
-    extern template cudaError_t launch_sweep<T, C, 128, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
-    extern template cudaError_t launch_sweep<T, C, 256, 4>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
-    extern template cudaError_t launch_sweep_capacity<T, C, 128, 4>(int, size_t, int*);                            \
-    extern template cudaError_t launch_sweep_capacity<T, C, 256, 4>(int, size_t, int*);
-LB_SWEEP_EXTERN(float, float)
-LB_SWEEP_EXTERN(__nv_bfloat16, float)
-LB_SWEEP_EXTERN(double, double)
+#define LB_SWEEP_EXTERN(T, C, NX)                                                                                   \
+    extern template cudaError_t launch_sweep<T, C, 128, 4, NX>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_sweep<T, C, 256, 4, NX>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_sweep_capacity<T, C, 128, 4, NX>(int, size_t, int*);                            \
+    extern template cudaError_t launch_sweep_capacity<T, C, 256, 4, NX>(int, size_t, int*);
+LB_SWEEP_EXTERN(float, float, 0)
+LB_SWEEP_EXTERN(__nv_bfloat16, float, 0)
+LB_SWEEP_EXTERN(double, double, 0)
+LB_SWEEP_EXTERN(float, float, 4)
+LB_SWEEP_EXTERN(__nv_bfloat16, float, 4)
+LB_SWEEP_EXTERN(double, double, 4)
 #undef LB_SWEEP_EXTERN
 #define LB_SWEEP_SMEM_EXTERN(T, C, NX)                                                                                   \
     extern template cudaError_t launch_sweep_smem<T, C, 128, 4, NX>(const SweepArgs<T, C>&, int, int, size_t, cudaStream_t); \
@@ -1150,6 +1153,10 @@ cudaError_t sweep_launch(lb_handle* h, const SweepGroup& g, int var, int nt, int
         return launch_sweep_smem<T, C, 256, kSweepNPT>(a, g.count, cl, smem, stream);
     }
     const size_t smem = sweep_smem(h, g.ny_max, cl);
+    if (h->nx == 4) {
+        if (nt == 128) return launch_sweep<T, C, 128, kSweepNPT, 4>(a, g.count, cl, smem, stream);
+        return launch_sweep<T, C, 256, kSweepNPT, 4>(a, g.count, cl, smem, stream);
+    }
     if (nt == 128) return launch_sweep<T, C, 128, kSweepNPT>(a, g.count, cl, smem, stream);
     return launch_sweep<T, C, 256, kSweepNPT>(a, g.count, cl, smem, stream);
 }
@@ -1179,6 +1186,9 @@ int sweep_capacity(lb_handle* h, const SweepGroup& g, int var, int nt, int cl) {
                                  : launch_sweep_smem_capacity<T, C, 256, kSweepNPT>(cl, smem, &n);
             }
             const size_t smem = sweep_smem(h, g.ny_max, cl);
+            if (h->nx == 4)
+                return nt == 128 ? launch_sweep_capacity<T, C, 128, kSweepNPT, 4>(cl, smem, &n)
+                                 : launch_sweep_capacity<T, C, 256, kSweepNPT, 4>(cl, smem, &n);
             return nt == 128 ? launch_sweep_capacity<T, C, 128, kSweepNPT>(cl, smem, &n)
                              : launch_sweep_capacity<T, C, 256, kSweepNPT>(cl, smem, &n);
         }

@@ -70,14 +70,16 @@ __device__ __forceinline__ void pull9_l2(const T* __restrict__ pc, long long P, 
 
 // NT threads per CTA; each thread owns up to NPT nodes of the CTA's rows (host guarantees
 // rows * nx <= NT * NPT).
-template <typename T, typename C, int NT, int NPT>
-__global__ void __launch_bounds__(NT) k_sweep(const SweepArgs<T, C> a) {
+// NX > 0: the handle's width as a compile-time constant (shifts and masks in the node index
+// arithmetic for NX = 4); NX = 0: any width.  FP32 arithmetic is bounded to 128 registers.
+template <typename T, typename C, int NT, int NPT, int NX = 0>
+__global__ void __launch_bounds__(NT, sizeof(C) == 8 ? 1 : 512 / NT) k_sweep(const SweepArgs<T, C> a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int CL = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int ch = a.order[blockIdx.x / CL];
     const ChanParams<C> P = a.chan[ch];
-    const int nx = a.nx, ny = P.ny, t = threadIdx.x;
+    const int nx = NX > 0 ? NX : a.nx, ny = P.ny, t = threadIdx.x;
     const int y0 = (int)((long long)ny * rank / CL), y1 = (int)((long long)ny * (rank + 1) / CL);
     const int ey0 = max(y0 - 2, 0), ey1 = min(y1 + 2, ny);  // rows whose gradient velocity we need
     const int n_own = (y1 - y0) * nx, n_ext = (ey1 - ey0) * nx;
@@ -224,9 +226,9 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs<T, C> a) {
 
 // How many clusters of `cl` CTAs with `smem` bytes the device can hold at once (0: the shape cannot
 // be co-scheduled, so it is never launched).
-template <typename T, typename C, int NT, int NPT>
+template <typename T, typename C, int NT, int NPT, int NX = 0>
 cudaError_t launch_sweep_capacity(int cl, size_t smem, int* n_clusters) {
-    auto k = k_sweep<T, C, NT, NPT>;
+    auto k = k_sweep<T, C, NT, NPT, NX>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -245,9 +247,9 @@ cudaError_t launch_sweep_capacity(int cl, size_t smem, int* n_clusters) {
     return cudaOccupancyMaxActiveClusters(n_clusters, k, &cfg);
 }
 
-template <typename T, typename C, int NT, int NPT>
+template <typename T, typename C, int NT, int NPT, int NX = 0>
 cudaError_t launch_sweep(const SweepArgs<T, C>& a, int n_clusters, int cl, size_t smem, cudaStream_t s) {
-    auto k = k_sweep<T, C, NT, NPT>;
+    auto k = k_sweep<T, C, NT, NPT, NX>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     // set every time: an earlier capacity query may have left a smaller limit
