@@ -177,16 +177,19 @@ lb_status lb_monitor(lb_handle *h, double *out);
 enum { LB_MONITOR_RESIDUAL = 0, LB_MONITOR_FLUX_MAX = 1 };
 lb_status lb_set_monitor_mode(lb_handle *h, int mode);
 
-/* The same diagnostics without waiting: enqueues their copy into out ([n_channels][4], pinned
- * host memory or device memory) on the handle's stream and returns at once.  The values are
- * there when the stream has passed this point (cudaStreamSynchronize, or an event recorded after
- * the call); a monitoring loop can read step k's diagnostics while step k+1 runs.  LB_ESTATE if
- * no residual has been evaluated yet. */
+/* The same diagnostics without waiting: enqueues their transfer into out ([n_channels][4], pinned
+ * host memory or device memory) on the handle's stream and returns at once.  Pinned host memory
+ * mapped into the device's address space (cudaHostAlloc, or any pinned allocation under unified
+ * addressing) is written by a one-block kernel, anything else by a stream-ordered copy.  The values
+ * are there when the stream has passed this point (cudaStreamSynchronize, or an event recorded
+ * after the call); a monitoring loop can read step k's diagnostics while step k+1 runs.
+ * LB_ESTATE if no residual has been evaluated yet. */
 lb_status lb_monitor_async(lb_handle *h, double *out);
 
 /* Change the body force of one channel (channel = -1: all), e.g. 0 for cessation.  Stream-
- * ordered: the force goes host -> device from pinned memory and applies to every step enqueued
- * after this call; the call does not wait for the steps enqueued before it. */
+ * ordered: the force is staged in mapped pinned memory, which a small kernel on the handle's stream
+ * reads and applies to every step enqueued after this call; the call does not wait for the steps
+ * enqueued before it (a ring of 8 staging slots: it waits only when the host is 8 changes ahead). */
 lb_status lb_set_body_force(lb_handle *h, int channel, double g_x);
 
 /* Set the velocity of the moving wall of one channel (channel = -1: all) of a LB_WALLS_COUETTE
