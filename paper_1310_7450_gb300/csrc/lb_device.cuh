@@ -32,6 +32,11 @@ __host__ __device__ constexpr C wgt(int i) {
 }
 
 // ---- storage precision ---------------------------------------------------------------------
+// Two-component vector of an arithmetic type (8- or 16-byte accesses of (x, y) pairs).
+template <typename C> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
 template <typename T> struct Store;
 template <> struct Store<double> {
     using C = double;

@@ -342,11 +342,16 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
                 if (r == ny - 1 && a.chan[0].moving) zou_he_top<C>(d, a.chan[0].u_wall);
             }
         };
+        // the ring holds (u_x, u_y) pairs at even offsets from a 128-byte aligned base: one
+        // 8-byte shared access per pair
+        using V2 = typename Vec2<C>::type;
         auto put_u = [&](int r, int col, C ux, C uy) {
-            C* u = uring + 2 * ((r & 3) * UW + col + 1);
-            u[0] = ux;
-            u[1] = uy;
+            V2 v;
+            v.x = ux;
+            v.y = uy;
+            *reinterpret_cast<V2*>(uring + 2 * ((r & 3) * UW + col + 1)) = v;
         };
+        auto get_u = [&](const C* p) -> V2 { return *reinterpret_cast<const V2*>(p); };
         auto moments_row = [&](int r, C (&d)[NC][9], C (&dR)[NC], C (&jx)[NC], C (&jy)[NC]) {
             // own columns, then the two halo columns (threads 0 and 1)
             if (r >= 0 && r < ny) {
@@ -502,22 +507,25 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
                 for (int c = 0; c < NC; ++c) {
                     const int col = col0 + c;
                     const C* uc = uring + 2 * ((y & 3) * UW + col + 1);
-                    const C ka = C(0.5) * (uc[2] - uc[-2]);
-                    const C kc = C(0.5) * (uc[3] - uc[-1]);
+                    const V2 ue = get_u(uc + 2), uw = get_u(uc - 2);  // columns col+1, col-1
+                    const C ka = C(0.5) * (ue.x - uw.x);
+                    const C kc = C(0.5) * (ue.y - uw.y);
                     C kb, ke;
-                    const C* up = uring + 2 * (((y + 1) & 3) * UW + col + 1);
-                    const C* um = uring + 2 * (((y + 3) & 3) * UW + col + 1);  // row y-1
+                    const V2 un = get_u(uring + 2 * (((y + 1) & 3) * UW + col + 1));  // row y+1
+                    const V2 us = get_u(uring + 2 * (((y + 3) & 3) * UW + col + 1));  // row y-1
                     if (y == 0) {
-                        const C* up2 = uring + 2 * (((y + 2) & 3) * UW + col + 1);
-                        kb = C(0.5) * (C(-3) * uc[0] + C(4) * up[0] - up2[0]);
-                        ke = C(0.5) * (C(-3) * uc[1] + C(4) * up[1] - up2[1]);
+                        const V2 u0 = get_u(uc);
+                        const V2 un2 = get_u(uring + 2 * (((y + 2) & 3) * UW + col + 1));
+                        kb = C(0.5) * (C(-3) * u0.x + C(4) * un.x - un2.x);
+                        ke = C(0.5) * (C(-3) * u0.y + C(4) * un.y - un2.y);
                     } else if (y == ny - 1) {
-                        const C* um2 = uring + 2 * (((y + 2) & 3) * UW + col + 1);  // row y-2
-                        kb = C(0.5) * (C(3) * uc[0] - C(4) * um[0] + um2[0]);
-                        ke = C(0.5) * (C(3) * uc[1] - C(4) * um[1] + um2[1]);
+                        const V2 u0 = get_u(uc);
+                        const V2 us2 = get_u(uring + 2 * (((y + 2) & 3) * UW + col + 1));  // row y-2
+                        kb = C(0.5) * (C(3) * u0.x - C(4) * us.x + us2.x);
+                        ke = C(0.5) * (C(3) * u0.y - C(4) * us.y + us2.y);
                     } else {
-                        kb = C(0.5) * (up[0] - um[0]);
-                        ke = C(0.5) * (up[1] - um[1]);
+                        kb = C(0.5) * (un.x - us.x);
+                        ke = C(0.5) * (un.y - us.y);
                     }
                     const NodeState<C> s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dRc[c], jxc[c], jyc[c], drho_prev[c],
                                                                   so_xx[c], so_xy[c], so_yy[c]);
