@@ -342,8 +342,9 @@ int lb_uses_row_march(const lb_handle *h);  /* 1 if plain steps run on the row-m
 /* Work items of the row-march kernel for a single nx x ny channel (host only, no GPU needed):
  * strips of 128 columns cut into row ranges, at most one per resident CTA (ctas_per_sm x n_sm),
  * with rows dealt so that every item is expected to take the same time (later CTAs on an SM run
- * slower under the warp schedulers' age priority; the two edge strips cost more per row).  FP32
- * plans give all interior strips the same row boundaries (their halo reads then hit L2).
+ * slower under the warp schedulers' age priority; the two edge strips cost more per row).  Grids
+ * of three or more strips give all interior strips the same row boundaries (their halo reads then
+ * hit L2).
  * precision LB_PREC_F32 or LB_PREC_BF16, gpbc nonzero for pressure-driven ends (the model's edge
  * cost depends on both).  Writes (x0, y0, y1) per item into items[3 * max_items] (caller-owned
  * host memory; items may be NULL to query the count) and returns the number of items, or

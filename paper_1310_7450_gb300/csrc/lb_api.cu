@@ -580,7 +580,8 @@ bool make_pop_map(const lb_handle* h, void* base, CUtensorMap* map) {
 //    boundaries -- row chunk c of every interior strip on consecutive blocks, T times the speed of
 //    the slowest of them in rows -- so neighbouring strips march the same rows at the same time
 //    and read each other's halo columns from L2 (with boundaries that differ between strips, BF16
-//    re-reads 9 DRAM bytes per node of halo).
+//    re-reads 9 DRAM bytes per node of halo).  Both precisions are dealt chunk-major; strip-major
+//    serves grids of one or two strips.
 // Items keep at least 8 rows on average (at most ny / 8 per strip).
 struct MarchModel {
     double skew, fedge;
@@ -592,11 +593,13 @@ struct MarchModel {
 //     against strip-major skew 0: 59.1 (strip-major with skew loses: 0.12 -> 55.5, the halo
 //     re-reads); f = 1.2; pressure-driven ends f = 1.5 with the edge strips first 53.6 (last: 50.3;
 //     strip-major 53.0); moving wall 59.1 (57.7); 8192 x 2048 58.2 (57.2); 2048 x 2048 52.6 (51.9).
-//   BF16 (issue-bound): strip-major skew 0.3: 74.7 (chunk-major 74.0); skew 0 / 0.12 / 0.2 / 0.28 /
-//     0.36 / 0.45 -> 73.7 / 75.2 / 75.6 / 75.9 / 76.1 / 73.6 with f = 1.09-1.2; pressure-driven
-//     ends f = 1.3 / 1.5 / 1.6 / 1.9 -> 62.2 / 65.6 / 64.8 / 63.6.
+//   BF16 (issue-bound): chunk-major skew 0.3: 75.4 (0.45: 75.1, 0.6: 74.0; with the edge strips on
+//     the last blocks 74.0) against strip-major skew 0.3: 74.6-74.7 (strip-major skew 0 / 0.12 / 0.2 /
+//     0.28 / 0.36 / 0.45 -> 73.7 / 75.2 / 75.6 / 75.9 / 76.1 / 73.6 on another GPU); f = 1.15;
+//     pressure-driven ends f = 1.5 (65.55; strip-major 65.45; f = 1.3 / 1.6 / 1.9 strip-major ->
+//     62.2 / 64.8 / 63.6).
 static MarchModel march_model(int prec, bool gpbc) {
-    if (prec == LB_PREC_BF16) return {0.30, gpbc ? 1.5 : 1.15, false};
+    if (prec == LB_PREC_BF16) return {0.30, gpbc ? 1.5 : 1.15, true};
     return {0.12, gpbc ? 1.5 : 1.2, true};
 }
 

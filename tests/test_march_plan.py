@@ -37,9 +37,9 @@ def test_items_tile_every_strip_once(nx, ny, R, prec, gpbc):
     for x0 in range(0, nx, 128):
         y = it[it[:, 0] == x0][:, 1]
         assert np.all(np.diff(y) > 0)
-    if prec == "f32" and 3 <= strips < R * NSM:
-        # FP32 is dealt chunk-major: the interior strips share their row boundaries (neighbouring
-        # strips march the same rows together and read each other's halo columns from L2)
+    if 3 <= strips < R * NSM:
+        # dealt chunk-major: the interior strips share their row boundaries (neighbouring strips
+        # march the same rows together and read each other's halo columns from L2)
         b = [tuple(it[it[:, 0] == x0][:, 1]) for x0 in range(128, nx - 128, 128)]
         assert all(bb == b[0] for bb in b)
 
