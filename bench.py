@@ -52,10 +52,15 @@ def kernel_hash(kernel: str) -> str:
 PREC_NAME = {"f32": "FP32", "bf16": "BF16", "f64": "FP64"}
 
 
-def bytes_per_node(precision: str, store_sigma: bool, stress_mode: int) -> int:
+def bytes_per_node(precision: str, store_sigma: bool, stress_mode: int, scheme: str = "paper") -> int:
     """Algorithmic HBM bytes per node and step: 9 population loads + 9 stores in the storage type,
     delta rho read + write, (+ stress write: xx, yy, xy -- the zz plane of the 4-component stress is
-    0 in 2-D flow and written once at create), (+ carried stress read + write in stress mode 1)."""
+    0 in 2-D flow and written once at create), (+ carried stress read + write in stress mode 1).
+    Comparison schemes of Sec. II C and the relaxation-time extensions (tile kernel): the
+    generalized-Newtonian scheme moves the same bytes; the stress-divergence scheme runs a first
+    pass that reads the populations and delta rho and writes Sigma^nN (3 planes), then the step,
+    which also reads Sigma^nN; the relaxation model with a fluidity memory reads and writes the
+    FP64 fluidity plane."""
     t = {"f64": 8, "f32": 4, "bf16": 2}[precision]
     c = 8 if precision == "f64" else 4
     b = 18 * t + 2 * c
@@ -63,6 +68,10 @@ def bytes_per_node(precision: str, store_sigma: bool, stress_mode: int) -> int:
         b += 3 * c
     if stress_mode == 1:
         b += 6 * c
+    if scheme == "stress_divergence":
+        b += 9 * t + c + 3 * c + 3 * c   # first pass: populations + delta rho in, Sigma^nN out; step: Sigma^nN in
+    elif scheme == "relaxation":
+        b += 16                          # fluidity plane (FP64) read + write
     return b
 
 
@@ -220,14 +229,21 @@ def run_gpu(args):
     flags = lbnlm.LB_GRID_STORE_SIGMA if args.store_sigma else 0
     if args.tile_only:
         flags |= lbnlm.LB_GRID_TILE_ONLY
+    if args.scheme == "relaxation":
+        flags |= lbnlm.LB_GRID_RELAXATION_MODEL
+    lib_scheme = args.scheme if args.scheme in lbnlm.SCHEME_FLAGS else "paper"
     sim = lbnlm.Channels(nx, ny, p, args.precision, stress_mode=args.stress_mode, flags=flags,
-                         stream=stream.cuda_stream, x_mode=args.x_mode, walls=args.walls)
+                         stream=stream.cuda_stream, x_mode=args.x_mode, walls=args.walls, scheme=lib_scheme)
     if args.walls == "couette":
         lbnlm.lb_set_wall_velocity(sim.h, -1, args.u_wall)
+    if args.scheme == "relaxation":
+        # density-dependent Maxwell time and a fluidity memory of tau_M (both extensions at once)
+        lbnlm.lb_set_relaxation_model(sim.h, -1, 5.0, 1.0, 2000.0)
     nodes = nx * ny
     kernel = "k_step_march" if lbnlm.lb_uses_row_march(sim.h) else "k_step_tile"
-    # pressure-driven ends add one boundary-column kernel before every step (either step kernel)
-    launches_per_step = 2 if args.x_mode == "gpbc" else 1
+    # pressure-driven ends add one boundary-column kernel before every step (either step kernel);
+    # the stress-divergence scheme runs two passes of the tile kernel per step
+    launches_per_step = (2 if args.x_mode == "gpbc" else 1) * (2 if args.scheme == "stress_divergence" else 1)
 
     def barrier():
         if ws > 1:
@@ -325,7 +341,7 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return 0
     peak, peak_kind = measured_peaks()
-    bpn = bytes_per_node(args.precision, args.store_sigma, args.stress_mode)
+    bpn = bytes_per_node(args.precision, args.store_sigma, args.stress_mode, args.scheme)
     achieved = bpn * nodes / (ms_step * 1e-3) / 1e9
     traffic = stored_traffic(kernel, args.precision, nodes)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -346,7 +362,7 @@ def run_gpu(args):
                                    + (" + 4-component stress" if args.store_sigma else "")
                                    + ("" if args.x_mode == "periodic" else "; pressure-driven ends (GPBC)")
                                    + ("" if args.walls == "bounce_back" else f"; Couette wall u={args.u_wall:g}"),
-                       "x_mode": args.x_mode, "walls": args.walls, "kernel": kernel,
+                       "x_mode": args.x_mode, "walls": args.walls, "scheme": args.scheme, "kernel": kernel,
                        "nx": nx, "ny": ny, "precision": args.precision, "stress_mode": args.stress_mode,
                        "store_sigma": bool(args.store_sigma),
                        "l2": f"state {bpn * nodes / 2**30:.2f} GiB per step, larger than the 126 MB L2 (no flush)",
@@ -701,6 +717,8 @@ def main():
     ap.add_argument("--walls", default="bounce_back", choices=["bounce_back", "couette"])
     ap.add_argument("--u-wall", type=float, default=0.01)
     ap.add_argument("--tile-only", action="store_true")
+    ap.add_argument("--scheme", default="paper",
+                    choices=["paper", "generalized_newtonian", "stress_divergence", "relaxation"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-train", type=int, default=2000)
