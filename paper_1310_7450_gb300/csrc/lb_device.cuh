@@ -395,10 +395,14 @@ __device__ __forceinline__ C relaxation_time_ext(const ChanParams<C>& P, C ka, C
     const C sII = Arith<C>::sqrt(C(0.5) * (Dxx * Dxx + C(2) * Dxy * Dxy + Dyy * Dyy));
     *phi = 0.0;
     if (P.tau_f > C(0) && tau > C(0)) {
-        const double phi_ss = 1.0 / (double)tau + (double)sII * (double)P.inv_gc;
-        const double tf = (double)P.tau_f;
-        *phi = phi_old > 0.0 ? (tf * phi_old + phi_ss) / (tf + 1.0) : phi_ss;
-        return (C)(1.0 / *phi);
+        // 1/tau and the weight 1/(tau_f + 1) are formed in the arithmetic type (the FP32 reciprocal
+        // in the FP32 modes: FP64 divisions on this part would bound the step), the recursion in FP64
+        // as an increment, phi = phi_old + (phi_ss - phi_old) / (tau_f + 1) -- the same backward
+        // Euler step, whose fixed point is phi_ss exactly whatever the rounding of the weight
+        const double phi_ss = (double)Arith<C>::div(C(1), tau) + (double)sII * (double)P.inv_gc;
+        const double w = (double)Arith<C>::div(C(1), P.tau_f + C(1));
+        *phi = phi_old > 0.0 ? phi_old + (phi_ss - phi_old) * w : phi_ss;
+        return Arith<C>::div(C(1), (C)*phi);
     }
     return Arith<C>::div(tau, C(1) + tau * sII * P.inv_gc);
 }
