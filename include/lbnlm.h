@@ -58,7 +58,9 @@ enum { LB_STRESS_INLM = 0, LB_STRESS_TIMESTEPPED = 1 };
  * plain tile-kernel steps from a captured CUDA graph: the same kernels with the same arguments,
  * bitwise the same result, without the per-launch host overhead).
  * The comparison schemes of Sec. II C (the usual alternatives to the paper's forcing; at most one,
- * stress mode 0, periodic x and bounce-back walls, tile kernel, not in lb_run_until_steady):
+ * stress mode 0, periodic x and bounce-back walls, not in lb_run_until_steady; the
+ * generalized-Newtonian scheme runs on the row-march kernel for wide single FP32/BF16 channels,
+ * the divergence scheme on the tile kernel):
  * LB_GRID_GENERALIZED_NEWTONIAN relaxes each node with tau_LB(gdot) = 1/2 + eta_eff/(rho0 c_s^2)
  * (Eq. taulb with the model's steady-shear viscosity eta_eff = G_inf tau_M + G_inf tau0, tau_M of
  * Eq. nlmaxwell at the node's shear rate) and keeps only the body-force terms of Eq. (bodyforce);

@@ -1,4 +1,5 @@
-// Instantiation of the TMA-fed row-march step (wide single channels; FP32 and BF16 storage).
+// Instantiation of the TMA-fed row-march step (wide single channels; FP32 and BF16 storage; the
+// paper's scheme in both stress modes and the generalized-Newtonian comparison scheme).
 #include "lb_step_march.cuh"
 
 namespace lbk {
@@ -10,4 +11,9 @@ template cudaError_t march_occupancy<float, float, 0>(int*);
 template cudaError_t march_occupancy<float, float, 1>(int*);
 template cudaError_t march_occupancy<__nv_bfloat16, float, 0>(int*);
 template cudaError_t march_occupancy<__nv_bfloat16, float, 1>(int*);
+// the generalized-Newtonian comparison scheme (stress mode A, periodic x, bounce-back walls)
+template cudaError_t launch_step_march<float, float, 0, 0, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+template cudaError_t launch_step_march<__nv_bfloat16, float, 0, 0, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+template cudaError_t march_occupancy<float, float, 0, 0, 1>(int*);
+template cudaError_t march_occupancy<__nv_bfloat16, float, 0, 0, 1>(int*);
 }  // namespace lbk

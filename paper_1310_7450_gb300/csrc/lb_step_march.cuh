@@ -186,7 +186,9 @@ __device__ __forceinline__ void store_cols_pop(T* po, long long P, const C (&d)[
 #ifndef LBK_MARCH_MINB2
 #define LBK_MARCH_MINB2 7
 #endif
-template <typename T, typename C, int SMODE, int CW, int NC, int K, int BND = 0>
+// SCHEME 1: the generalized-Newtonian comparison scheme of Sec. II C (periodic x, bounce-back
+// walls, stress mode A), the node's own relaxation rate as in the tile kernel's scheme-1 variant.
+template <typename T, typename C, int SMODE, int CW, int NC, int K, int BND = 0, int SCHEME = 0>
 __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step_march(const __grid_constant__ CUtensorMap tmap,
                                                           const StepArgs<T, C> a, const MarchCtl ctl) {
     constexpr int NT = CW / NC;                                      // threads per CTA
@@ -527,11 +529,18 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
                         kb = C(0.5) * (un.x - us.x);
                         ke = C(0.5) * (un.y - us.y);
                     }
-                    const NodeState<C> s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dRc[c], jxc[c], jyc[c], drho_prev[c],
-                                                                  so_xx[c], so_xy[c], so_yy[c]);
+                    NodeState<C> s;
+                    C om_n = P.omega;
+                    if constexpr (SCHEME == 1) {
+                        s = constitutive_gn<C>(P, ka, kb, kc, ke, dRc[c], jxc[c], jyc[c], &om_n);
+                    } else {
+                        s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dRc[c], jxc[c], jyc[c], drho_prev[c], so_xx[c],
+                                                   so_xy[c], so_yy[c]);
+                    }
                     const C rho_h = C(1) + s.dReq - s.drho;
                     vbad |= !velocity_ok<C>(jxc[c], jyc[c], rho_h, a.guard);  // NaN or too fast
-                    collide_node<C>(P, s, dcur[c], D[c]);
+                    if constexpr (SCHEME == 1) collide_impl<C, true>(P, s, dcur[c], D[c], om_n, C(1) - C(0.5) * om_n, P.gx, C(0));
+                    else collide_node<C>(P, s, dcur[c], D[c]);
                     sxx[c] = s.sxx;
                     syy[c] = s.syy;
                     sxy[c] = s.sxy;
@@ -661,11 +670,11 @@ constexpr int kMarchK = 8;    // shared-memory row slots (copies run K-2 rows ah
 template <typename T, int BND>
 constexpr int march_nc() { return std::is_same<T, __nv_bfloat16>::value ? LBK_MARCH_NC_BF16 : 1; }
 
-template <typename T, typename C, int SMODE, int BND = 0>
+template <typename T, typename C, int SMODE, int BND = 0, int SCHEME = 0>
 cudaError_t launch_step_march(const CUtensorMap& map, const StepArgs<T, C>& a, const MarchCtl& ctl, int grid,
                               cudaStream_t s) {
     constexpr int NC = march_nc<T, BND>();
-    auto k = k_step_march<T, C, SMODE, kMarchW, NC, kMarchK, BND>;
+    auto k = k_step_march<T, C, SMODE, kMarchW, NC, kMarchK, BND, SCHEME>;
     const size_t smem = march_smem_bytes<T, C, kMarchW, kMarchK>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -674,10 +683,10 @@ cudaError_t launch_step_march(const CUtensorMap& map, const StepArgs<T, C>& a, c
     return cudaGetLastError();
 }
 
-template <typename T, typename C, int SMODE, int BND = 0>
+template <typename T, typename C, int SMODE, int BND = 0, int SCHEME = 0>
 cudaError_t march_occupancy(int* blocks_per_sm) {
     constexpr int NC = march_nc<T, BND>();
-    auto k = k_step_march<T, C, SMODE, kMarchW, NC, kMarchK, BND>;
+    auto k = k_step_march<T, C, SMODE, kMarchW, NC, kMarchK, BND, SCHEME>;
     const size_t smem = march_smem_bytes<T, C, kMarchW, kMarchK>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

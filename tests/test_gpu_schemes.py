@@ -127,6 +127,38 @@ def test_comparison_schemes_are_refused_where_not_implemented(stream):
         with pytest.raises(lbnlm.LBError) as e:
             sim.run_until_steady(1e-8, check_every=100, max_steps=200)
         assert e.value.status == lbnlm.LB_EINVAL
-    # wide FP32 channels of the comparison schemes stay on the tile kernel
+    # wide FP32 channels: the generalized-Newtonian scheme has a row-march variant, the divergence
+    # scheme (two passes per step) stays on the tile kernel
     with lbnlm.Channels(256, 32, p, "f32", stream=stream, scheme="generalized_newtonian") as sim:
+        assert lbnlm.lb_uses_row_march(sim.h)
+    with lbnlm.Channels(256, 32, p, "f32", stream=stream, scheme="stress_divergence") as sim:
         assert not lbnlm.lb_uses_row_march(sim.h)
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_generalized_newtonian_row_march_equals_tile_kernel_and_oracle(stream, prec):
+    """Wide single FP32/BF16 channels of the generalized-Newtonian scheme step on the row-march
+    kernel's scheme variant: bitwise equal to the tile kernel's, and in FP32 within 1e-5 of the
+    oracle on u (BF16: a few units of its roundoff 2^-9)."""
+    nx, ny = 256, 48
+    scheme = "generalized_newtonian"
+    p = dict(nlm(), scheme=scheme)
+    st = random_state(nx, ny, 901, amp=1e-3)
+    res = {}
+    for flags in (0, lbnlm.LB_GRID_TILE_ONLY):
+        with lbnlm.Channels(nx, ny, p, prec, flags=flags | lbnlm.LB_GRID_STORE_SIGMA, stream=stream,
+                            scheme=scheme) as sim:
+            assert lbnlm.lb_uses_row_march(sim.h) == (flags == 0)
+            sim.set_populations([st.nstar], [st.drho])
+            sim.step(40)
+            (u, s, r), = sim.fields()
+            (n, d), = sim.populations()
+            res[flags] = (u, s, n, d)
+    u_m, s_m, n_m, d_m = res[0]
+    u_t, s_t, n_t, d_t = res[lbnlm.LB_GRID_TILE_ONLY]
+    assert np.array_equal(n_m, n_t) and np.array_equal(u_m, u_t) and np.array_equal(s_m, s_t)
+    assert np.all(d_m == 0.0)
+    oracle.run(p, st, 40)
+    u_o, s_o, _ = oracle.fields(p, st)
+    print(f"{prec} row march GN vs oracle: u {rel(u_m, u_o):.2e}, sigma {rel(s_m, s_o):.2e}")
+    assert rel(u_m, u_o) < (1e-5 if prec == "f32" else 4 * 2.0 ** -9)
