@@ -71,7 +71,9 @@ enum { LB_STRESS_INLM = 0, LB_STRESS_TIMESTEPPED = 1 };
  * flow-induced density (two launches per step).  Both have delta rho = 0.
  * LB_GRID_RELAXATION_MODEL keeps the paper's scheme and enables the relaxation-time extensions of
  * its outlook (lb_set_relaxation_model; off until set): FP64, FP32 or BF16, either stress mode,
- * any boundary, tile kernel, not in lb_run_until_steady; one more plane per node (the fluidity). */
+ * any boundary, not in lb_run_until_steady; one more plane per node (the fluidity).  Wide single
+ * FP32/BF16 channels with periodic x and bounce-back walls step on the row-march kernel's variant,
+ * the others on the tile kernel. */
 enum { LB_GRID_STORE_SIGMA = 1, LB_GRID_TILE_ONLY = 2, LB_GRID_BF16_STOCHASTIC = 4, LB_GRID_NO_GRAPH = 8,
        LB_GRID_GENERALIZED_NEWTONIAN = 16, LB_GRID_STRESS_DIVERGENCE = 32, LB_GRID_RELAXATION_MODEL = 64 };
 

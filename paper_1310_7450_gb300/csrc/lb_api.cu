@@ -100,6 +100,14 @@ extern template cudaError_t launch_step_march<float, float, 0, 0, 1>(const CUten
 extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0, 0, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t march_occupancy<float, float, 0, 0, 1>(int*);
 extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0, 0, 1>(int*);
+extern template cudaError_t launch_step_march<float, float, 0, 0, 3>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<float, float, 1, 0, 3>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0, 0, 3>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t launch_step_march<__nv_bfloat16, float, 1, 0, 3>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
+extern template cudaError_t march_occupancy<float, float, 0, 0, 3>(int*);
+extern template cudaError_t march_occupancy<float, float, 1, 0, 3>(int*);
+extern template cudaError_t march_occupancy<__nv_bfloat16, float, 0, 0, 3>(int*);
+extern template cudaError_t march_occupancy<__nv_bfloat16, float, 1, 0, 3>(int*);
 extern template cudaError_t launch_step_march<float, float, 0, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t launch_step_march<float, float, 1, 1>(const CUtensorMap&, const StepArgs<float, float>&, const MarchCtl&, int, cudaStream_t);
 extern template cudaError_t launch_step_march<__nv_bfloat16, float, 0, 1>(const CUtensorMap&, const StepArgs<__nv_bfloat16, float>&, const MarchCtl&, int, cudaStream_t);
@@ -707,7 +715,8 @@ static std::vector<MarchItem> march_plan(int nx, int ny, int R, int nsm, MarchMo
 lb_status plan_march(lb_handle* h) {
     h->march = false;
     if (h->n_ch != 1 || (h->prec != LB_PREC_F32 && h->prec != LB_PREC_BF16) || h->nx % kMarchW != 0 ||
-        h->ny[0] < 16 || (h->flags & LB_GRID_TILE_ONLY) || (h->scheme != 0 && h->scheme != 1))
+        h->ny[0] < 16 || (h->flags & LB_GRID_TILE_ONLY) || h->scheme == 2 ||
+        (h->scheme == 3 && (h->gpbc || h->moving)))
         return LB_OK;
     if (!make_pop_map(h, h->popA, &h->mapA) || !make_pop_map(h, h->popB, &h->mapB)) return LB_OK;
     h->mapA_buf = h->popA;
@@ -718,11 +727,13 @@ lb_status plan_march(lb_handle* h) {
         const bool bnd = h->gpbc || h->moving;
         if (h->prec == LB_PREC_F32) {
             if (h->scheme == 1) e = march_occupancy<float, float, 0, 0, 1>(&bps);
+            else if (h->scheme == 3) e = h->smode ? march_occupancy<float, float, 1, 0, 3>(&bps) : march_occupancy<float, float, 0, 0, 3>(&bps);
             else if (h->gpbc) e = h->smode ? march_occupancy<float, float, 1, 1>(&bps) : march_occupancy<float, float, 0, 1>(&bps);
             else if (bnd) e = h->smode ? march_occupancy<float, float, 1, 2>(&bps) : march_occupancy<float, float, 0, 2>(&bps);
             else e = h->smode ? march_occupancy<float, float, 1>(&bps) : march_occupancy<float, float, 0>(&bps);
         } else {
             if (h->scheme == 1) e = march_occupancy<__nv_bfloat16, float, 0, 0, 1>(&bps);
+            else if (h->scheme == 3) e = h->smode ? march_occupancy<__nv_bfloat16, float, 1, 0, 3>(&bps) : march_occupancy<__nv_bfloat16, float, 0, 0, 3>(&bps);
             else if (h->gpbc) e = h->smode ? march_occupancy<__nv_bfloat16, float, 1, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0, 1>(&bps);
             else if (bnd) e = h->smode ? march_occupancy<__nv_bfloat16, float, 1, 2>(&bps) : march_occupancy<__nv_bfloat16, float, 0, 2>(&bps);
             else e = h->smode ? march_occupancy<__nv_bfloat16, float, 1>(&bps) : march_occupancy<__nv_bfloat16, float, 0>(&bps);
@@ -943,6 +954,9 @@ cudaError_t launch_march<float, float>(lb_handle* h, const StepArgs<float, float
     march_monitor(h, a.flags, ctl);
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
     if (h->scheme == 1) return launch_step_march<float, float, 0, 0, 1>(m, a, ctl, h->march_grid, h->stream);
+    if (h->scheme == 3)
+        return h->smode ? launch_step_march<float, float, 1, 0, 3>(m, a, ctl, h->march_grid, h->stream)
+                        : launch_step_march<float, float, 0, 0, 3>(m, a, ctl, h->march_grid, h->stream);
     if (h->gpbc)
         return h->smode ? launch_step_march<float, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
                         : launch_step_march<float, float, 0, 1>(m, a, ctl, h->march_grid, h->stream);
@@ -958,6 +972,9 @@ cudaError_t launch_march<__nv_bfloat16, float>(lb_handle* h, const StepArgs<__nv
     march_monitor(h, a.flags, ctl);
     const CUtensorMap& m = ((const void*)a.pin == h->mapA_buf) ? h->mapA : h->mapB;
     if (h->scheme == 1) return launch_step_march<__nv_bfloat16, float, 0, 0, 1>(m, a, ctl, h->march_grid, h->stream);
+    if (h->scheme == 3)
+        return h->smode ? launch_step_march<__nv_bfloat16, float, 1, 0, 3>(m, a, ctl, h->march_grid, h->stream)
+                        : launch_step_march<__nv_bfloat16, float, 0, 0, 3>(m, a, ctl, h->march_grid, h->stream);
     if (h->gpbc)
         return h->smode ? launch_step_march<__nv_bfloat16, float, 1, 1>(m, a, ctl, h->march_grid, h->stream)
                         : launch_step_march<__nv_bfloat16, float, 0, 1>(m, a, ctl, h->march_grid, h->stream);

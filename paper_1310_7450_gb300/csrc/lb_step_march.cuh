@@ -188,8 +188,11 @@ __device__ __forceinline__ void store_cols_pop(T* po, long long P, const C (&d)[
 #endif
 // SCHEME 1: the generalized-Newtonian comparison scheme of Sec. II C (periodic x, bounce-back
 // walls, stress mode A), the node's own relaxation rate as in the tile kernel's scheme-1 variant.
+// SCHEME 3: the relaxation-time extensions (periodic x, bounce-back walls, either stress mode): the
+// node's FP64 fluidity is loaded one row ahead of its use and stored with the step, as in the tile
+// kernel's scheme-3 variant (the FP32 kernel then runs 4 CTAs per SM for the registers it needs).
 template <typename T, typename C, int SMODE, int CW, int NC, int K, int BND = 0, int SCHEME = 0>
-__global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step_march(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : (SCHEME == 3 ? 4 : 5)) k_step_march(const __grid_constant__ CUtensorMap tmap,
                                                           const StepArgs<T, C> a, const MarchCtl ctl) {
     constexpr int NT = CW / NC;                                      // threads per CTA
     constexpr int HP = MarchGeom<T>::HP;
@@ -414,6 +417,15 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
         C drho_next[NC], drho_next2[NC];
         load_cols<C, NC>(drow + (long long)y0 * nx, drho_next);
         if (y0 + 1 < y1) load_cols<C, NC>(drow + (long long)(y0 + 1) * nx, drho_next2);
+        // relaxation-time extensions with a fluidity memory: the node's fluidity (FP64), one row ahead
+        const bool fluid = SCHEME == 3 && P.tau_f > C(0);  // CTA-uniform
+        const double* phrow = a.phi + ctl.base + x;
+        double phi_cur[NC], phi_nxt[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) phi_cur[c] = phi_nxt[c] = 0.0;
+        if (fluid)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) phi_nxt[c] = phrow[(long long)y0 * nx + c];
         // on residual steps the saved velocity of each row is prefetched the same way, and one
         // thread brings the delta rho and saved-velocity rows into L2 four rows before their
         // register loads (a residual step reads 16 B more per node than a plain one, and the
@@ -469,6 +481,13 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
                 upy_cur[c] = upy_next[c];
             }
             if (y + 2 < y1) load_cols<C, NC>(drow + (long long)(y + 2) * nx, drho_next2);
+            if (fluid) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    phi_cur[c] = phi_nxt[c];
+                    if (y + 1 < y1) phi_nxt[c] = phrow[(long long)(y + 1) * nx + c];
+                }
+            }
             if (resid) {
                 if (t == TP) prefetch_rows(y + 6);
 #pragma unroll
@@ -533,13 +552,22 @@ __global__ void __launch_bounds__(CW / NC, NC == 2 ? LBK_MARCH_MINB2 : 5) k_step
                     C om_n = P.omega;
                     if constexpr (SCHEME == 1) {
                         s = constitutive_gn<C>(P, ka, kb, kc, ke, dRc[c], jxc[c], jyc[c], &om_n);
+                    } else if constexpr (SCHEME == 3) {
+                        double phi_new;
+                        const C tau_M = relaxation_time_ext<C>(P, ka, kb, kc, ke, dRc[c], drho_prev[c], phi_cur[c], &phi_new);
+                        s = constitutive<C, SMODE, true>(P, ka, kb, kc, ke, dRc[c], jxc[c], jyc[c], drho_prev[c], so_xx[c],
+                                                         so_xy[c], so_yy[c], tau_M);
+                        if (fluid) a.phi[ctl.base + pn + c] = phi_new;
                     } else {
                         s = constitutive<C, SMODE>(P, ka, kb, kc, ke, dRc[c], jxc[c], jyc[c], drho_prev[c], so_xx[c],
                                                    so_xy[c], so_yy[c]);
                     }
                     const C rho_h = C(1) + s.dReq - s.drho;
                     vbad |= !velocity_ok<C>(jxc[c], jyc[c], rho_h, a.guard);  // NaN or too fast
+                    // the schemes' variants call the collision exactly as the tile kernel's do (the
+                    // same expression, so the same contraction into fused multiply-adds)
                     if constexpr (SCHEME == 1) collide_impl<C, true>(P, s, dcur[c], D[c], om_n, C(1) - C(0.5) * om_n, P.gx, C(0));
+                    else if constexpr (SCHEME == 3) collide_impl<C, true>(P, s, dcur[c], D[c], P.omega, P.k2, P.gx, C(0));
                     else collide_node<C>(P, s, dcur[c], D[c]);
                     sxx[c] = s.sxx;
                     syy[c] = s.syy;

@@ -136,11 +136,48 @@ def test_relaxation_model_refusals(stream):
     with lbnlm.Channels(4, 16, p, "f32", stream=stream) as sim:
         with pytest.raises(lbnlm.LBError):
             lbnlm.lb_set_relaxation_model(sim.h, -1, 1.0, 1.0, 0.0)   # created without the flag
+    with lbnlm.Channels(256, 32, p, "f32", flags=RX, stream=stream, x_mode="gpbc") as sim:
+        assert not lbnlm.lb_uses_row_march(sim.h)   # (pressure-driven ends: the tile kernel)
     with lbnlm.Channels(256, 32, p, "f32", flags=RX, stream=stream) as sim:
-        assert not lbnlm.lb_uses_row_march(sim.h)
+        assert lbnlm.lb_uses_row_march(sim.h)
         for bad in ((0, 1.0, 0.0, 0.0), (0, 1.0, 1.0, -1.0), (5, 1.0, 1.0, 0.0)):
             with pytest.raises(lbnlm.LBError):
                 lbnlm.lb_set_relaxation_model(sim.h, *bad)
     with lbnlm.Channels(4, [16, 20], [p, p], "f32", flags=RX, stream=stream) as sim:
         with pytest.raises(lbnlm.LBError):
             sim.run_until_steady(1e-8, check_every=100, max_steps=200)
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("smode", [0, 1])
+def test_row_march_variant_equals_tile_kernel_and_oracle(stream, prec, smode):
+    """Wide single FP32/BF16 channels with the relaxation-time extensions (density-dependent tau and
+    a fluidity memory) step on the row-march kernel's scheme variant, whose fluidity is loaded a row
+    ahead: bitwise equal to the tile kernel (populations, fields and the fluidity through the
+    checkpoint image), and in FP32 within 1e-5 of the oracle on u."""
+    nx, ny, steps = 256, 40, 40
+    p = dict(inputs.matched_params(0.9, 10.0, 0.1, 1e-3, 1e-5), rho_pert_amp=1e-3, seed=9, stress_mode=smode,
+             beta_rho=2.0, rho_ref=1.0, tau_f=50.0)
+    res = {}
+    for flags in (0, lbnlm.LB_GRID_TILE_ONLY):
+        with lbnlm.Channels(nx, ny, p, prec, stress_mode=smode, flags=flags | RX | lbnlm.LB_GRID_STORE_SIGMA,
+                            stream=stream) as sim:
+            assert lbnlm.lb_uses_row_march(sim.h) == (flags == 0)
+            lbnlm.lb_set_relaxation_model(sim.h, -1, 2.0, 1.0, 50.0)
+            sim.step(steps)
+            (u, s, r), = sim.fields()
+            (n, d), = sim.populations()
+            buf = np.zeros(lbnlm.lb_state_bytes(sim.h), dtype=np.uint8)
+            lbnlm.lb_get_state(sim.h, buf)
+            res[flags] = (u, s, n, d, buf)
+    u_m, s_m, n_m, d_m, b_m = res[0]
+    u_t, s_t, n_t, d_t, b_t = res[lbnlm.LB_GRID_TILE_ONLY]
+    assert np.array_equal(n_m, n_t) and np.array_equal(d_m, d_t)
+    assert np.array_equal(u_m, u_t) and np.array_equal(s_m, s_t)
+    assert np.array_equal(b_m, b_t)              # (the image carries the fluidity plane)
+    if prec == "f32":
+        st = oracle.init_state(inputs.initial_density(nx, ny, 1.0, 1e-3, 9))
+        oracle.run(p, st, steps)
+        u_o, _, _ = oracle.fields(p, st)
+        print(f"relaxation row march {prec} smode {smode}: u {rel(u_m, u_o):.2e}")
+        assert rel(u_m, u_o) < 1e-5
