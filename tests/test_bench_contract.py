@@ -31,6 +31,19 @@ def test_bytes_per_node(prec, sigma, mode, expected):
     assert load_bench().bytes_per_node(prec, sigma, mode) == expected
 
 
+@pytest.mark.parametrize("prec,scheme,expected", [
+    ("f32", "paper", 92),
+    ("f32", "generalized_newtonian", 92),          # the same planes (delta rho stays 0)
+    # first pass: populations + delta rho read, Sigma^nN (3 planes) written; the step reads Sigma^nN
+    ("f32", "stress_divergence", 92 + 9 * 4 + 4 + 3 * 4 + 3 * 4),
+    ("f32", "relaxation", 92 + 16),                # the FP64 fluidity read and written
+    ("bf16", "relaxation", 56 + 16),
+    ("f64", "stress_divergence", 184 + 9 * 8 + 8 + 3 * 8 + 3 * 8),
+])
+def test_bytes_per_node_of_the_schemes(prec, scheme, expected):
+    assert load_bench().bytes_per_node(prec, True, 0, scheme) == expected
+
+
 def test_stored_traffic_is_tied_to_the_kernel_source():
     b = load_bench()
     assert b.stored_traffic("k_step_march", "no_such_precision", 1) is None
